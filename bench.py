@@ -1,0 +1,481 @@
+"""Benchmark of the compressed-matrix hot path on GB300.
+
+Default workload (one "step" = one pass of the whole hot path):
+  8192 x 8192 int64 count matrices A and B, entries Poisson(lambda = 5)
+  (seeds 1303 / 1304), x of length 8192 uniform over the signed 8-bit range,
+  s = 7.  Step: pack A, pack B, pack x (width selection + SM pack), unpack A
+  to int64, get 2^20 entries of A, C = A + B, D = 7 A, y = A x -- every result
+  re-packed at its exact width.  Inputs are generated on the GPU by the
+  library's counter-based generator (identical to the host generator used by
+  the tests) and stay resident; dense A and B (512 MiB each) are larger than
+  L2, so every step streams them from HBM.
+
+Printed: one JSON line (rank 0).  `value` is the step's algorithmic bytes
+(the one-pass traffic of each operation) divided by the
+device-timed step time, summed over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "compressed matvec GB/s (% HBM peak); packed matmul int-TOPS; batched vs plain"
+N_ROWS = N_COLS = 8192
+LAMBDA = 5.0
+SCALE = 7
+GET_COUNT = 1 << 20
+SEED_A, SEED_B = 1303, 1304
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="ccm_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [v.strip() for v in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax.append(float(p[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+class Workload:
+    """Device buffers and the step of the default workload (one rank)."""
+
+    def __init__(self, ccm, torch, dev, seed_offset: int):
+        import synth
+        self.ccm, self.torch, self.dev = ccm, torch, dev
+        n = N_ROWS * N_COLS
+        self.n = n
+        table = torch.from_numpy(synth.poisson_cdf_table(LAMBDA))
+        sa, sb = SEED_A + seed_offset, SEED_B + seed_offset
+        self.A = ccm.gen_poisson(n, sa, synth.STREAM_A, table, device=dev).view(N_ROWS, N_COLS)
+        self.B = ccm.gen_poisson(n, sb, synth.STREAM_B, table, device=dev).view(N_ROWS, N_COLS)
+        self.X = ccm.gen_uniform(N_COLS, sa, synth.STREAM_X, -128, 127, device=dev).view(N_COLS, 1)
+        self.idx = ccm.gen_uniform(GET_COUNT, sa, synth.STREAM_INDEX, 0, n - 1, device=dev)
+        self.seeds = (sa, sb)
+        ba, _ = ccm.measure(self.A)
+        bb, _ = ccm.measure(self.B)
+        bx, _ = ccm.measure(self.X)
+        self.pa = ccm.PackedMatrix(N_ROWS, N_COLS, ccm.words_for(N_ROWS, N_COLS, ba), dev)
+        self.pb = ccm.PackedMatrix(N_ROWS, N_COLS, ccm.words_for(N_ROWS, N_COLS, bb), dev)
+        self.px = ccm.PackedMatrix(N_COLS, 1, ccm.words_for(N_COLS, 1, bx), dev)
+        self.pc = ccm.PackedMatrix(N_ROWS, N_COLS, ccm.words_for(N_ROWS, N_COLS, max(ba, bb) + 2), dev)
+        self.pd = ccm.PackedMatrix(N_ROWS, N_COLS, ccm.words_for(N_ROWS, N_COLS, ba + 4), dev)
+        self.py = ccm.PackedMatrix(N_ROWS, 1, ccm.words_for(N_ROWS, 1, ba + bx + 15), dev)
+        self.unp = torch.empty((N_ROWS, N_COLS), dtype=torch.int64, device=dev)
+        self.got = torch.empty(GET_COUNT, dtype=torch.int64, device=dev)
+        self.err = torch.zeros(2, dtype=torch.int32, device=dev)
+        self.ws = ccm.workspace(ccm.OP_MATVEC, N_ROWS, N_COLS, 1, dev)
+        self.ma, self.mb, self.mx = self.pa.c(), self.pb.c(), self.px.c()
+        self.mc, self.md, self.my = self.pc.c(), self.pd.c(), self.py.c()
+        self.profiled = ["pack", "unpack", "add", "scale", "matvec"]
+        self.events = {k: [] for k in self.profiled}
+
+    def step(self, profile: bool = False, A=None, B=None, X=None):
+        """One pass of the hot path through the C ABI (asynchronous)."""
+        import ctypes
+        ccm, L = self.ccm, self.ccm.lib()
+        st = ctypes.c_void_p(self.torch.cuda.current_stream().cuda_stream)
+        A = self.A if A is None else A
+        B = self.B if B is None else B
+        X = self.X if X is None else X
+        by = ctypes.byref
+
+        def prof(name):
+            if profile:
+                e0 = self.torch.cuda.Event(enable_timing=True)
+                e1 = self.torch.cuda.Event(enable_timing=True)
+                ccm.profile_next(e0, e1)
+                self.events[name].append((e0, e1))
+
+        rc = []
+        prof("pack")
+        rc.append(L.ccm_pack(ctypes.c_void_p(A.data_ptr()), ccm.I64, N_ROWS, N_COLS, by(self.ma), st))
+        rc.append(L.ccm_pack(ctypes.c_void_p(B.data_ptr()), ccm.I64, N_ROWS, N_COLS, by(self.mb), st))
+        rc.append(L.ccm_pack(ctypes.c_void_p(X.data_ptr()), ccm.I64, N_COLS, 1, by(self.mx), st))
+        prof("unpack")
+        rc.append(L.ccm_unpack(by(self.ma), ctypes.c_void_p(self.unp.data_ptr()), ccm.I64,
+                               ctypes.c_void_p(self.err.data_ptr()), st))
+        rc.append(L.ccm_get(by(self.ma), ctypes.c_void_p(self.idx.data_ptr()), GET_COUNT,
+                            ctypes.c_void_p(self.got.data_ptr()),
+                            ctypes.c_void_p(self.err.data_ptr() + 4), st))
+        prof("add")
+        rc.append(L.ccm_add(by(self.ma), by(self.mb), by(self.mc), st))
+        prof("scale")
+        rc.append(L.ccm_scale(by(self.ma), SCALE, by(self.md), st))
+        prof("matvec")
+        rc.append(L.ccm_matvec(by(self.ma), by(self.mx), by(self.my),
+                               ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(), st))
+        if any(rc):
+            raise RuntimeError(f"C ABI returned {rc}")
+
+    def widths(self):
+        return {k: (p.header().width, p.header().is_signed) for k, p in
+                (("A", self.pa), ("B", self.pb), ("x", self.px), ("C", self.pc), ("D", self.pd),
+                 ("y", self.py))}
+
+    def check(self):
+        """Every output valid, and results consistent with the inputs."""
+        torch = self.torch
+        for p in (self.pa, self.pb, self.px, self.pc, self.pd, self.py):
+            p._written()
+            p.check()
+        assert int(self.err[0].item()) == 0 and int(self.err[1].item()) == 0
+        assert torch.equal(self.unp, self.A), "unpack(pack(A)) != A"
+        assert torch.equal(self.got, self.A.view(-1)[self.idx]), "get mismatch"
+        c = self.ccm.unpack(self.pc)
+        assert torch.equal(c, self.A + self.B), "add mismatch"
+        d = self.ccm.unpack(self.pd)
+        assert torch.equal(d, self.A * SCALE), "scale mismatch"
+        y = self.ccm.unpack(self.py).view(-1)
+        # int64 matvec reference on the GPU (exact: |y| < 2^40)
+        yr = (self.A.double() @ self.X.view(-1).double()).round().long()
+        assert torch.equal(y, yr), "matvec mismatch"
+
+    def step_bytes(self):
+        """Algorithmic (one-pass) bytes of each operation in a step."""
+        w = self.widths()
+        n, b = self.n, w["A"][0]
+        bb, bc, bd, bx, byw = w["B"][0], w["C"][0], w["D"][0], w["x"][0], w["y"][0]
+        ops = {
+            "pack": 8 * n + n * b / 8,                 # per matrix (A)
+            "pack_B": 8 * n + n * bb / 8,
+            "pack_x": 8 * N_COLS + N_COLS * bx / 8,
+            "unpack": n * b / 8 + 8 * n,
+            "get": GET_COUNT * (8 + 8 + 4),            # index, value, one word
+            "add": n * (b + bb + bc) / 8,
+            "scale": n * (b + bd) / 8,
+            "matvec": n * b / 8 + N_COLS * bx / 8 + N_ROWS * byw / 8,
+        }
+        return ops
+
+
+def kernel_traffic(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, when
+    the kernel source has not changed since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    import hashlib
+    for line in open(path):
+        p = line.split("#", 1)[0].split()
+        if len(p) >= 4 and p[0] == kernel:
+            src_hash = hashlib.sha256()
+            for f in p[3].split(","):
+                src_hash.update(open(os.path.join(ROOT, f), "rb").read())
+            if src_hash.hexdigest()[:16] == p[1]:
+                return float(p[2])
+    return None
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+
+    from paper_1303_0270_gb300 import ccm
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    ccm.lib()
+    wl = Workload(ccm, torch, dev, seed_offset=1000 * rank)
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        wl.step()
+    torch.cuda.synchronize()
+    wl.check()
+    widths = wl.widths()
+
+    sampler = ClockSampler(local_rank)
+    if rank == 0:
+        sampler.start()
+    barrier()
+    launches0 = ccm.launch_count()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        wl.step(profile=True)
+    t1.record()
+    barrier()
+    launches = ccm.launch_count() - launches0
+    ms = t0.elapsed_time(t1)
+    clocks = sampler.stop() if rank == 0 else None
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    wl.check()
+
+    # per-kernel times of the profiled main kernels
+    kern_ms = {k: statistics.mean(e0.elapsed_time(e1) for e0, e1 in v)
+               for k, v in wl.events.items() if v}
+    ops = wl.step_bytes()
+    step_bytes = sum(ops.values())
+    ms_per_step = ms / args.steps
+    value = world * step_bytes / (ms_per_step * 1e-3) / 1e9
+
+    # end to end: host (pinned) inputs in, results back to host, every step
+    e2e = run_e2e(wl, torch, args, barrier, dist, dev, world, step_bytes)
+
+    if rank != 0:
+        return None
+    hbm, peak_kind = peaks()
+    kernels = {"pack": "k_pack<ProdDenseI64>", "unpack": "k_unpack<int64_t>",
+               "add": "k_pack<ProdAdd>", "scale": "k_pack<ProdScale>",
+               "matvec": "k_matvec_rows"}
+    per_op = {}
+    for k, t in kern_ms.items():
+        gbs = ops[k] / (t * 1e-3) / 1e9
+        per_op[k] = {"kernel": kernels[k], "ms": round(t, 5), "algorithmic_bytes": int(ops[k]),
+                     "GB/s": round(gbs, 1), "frac_of_hbm": round(gbs / hbm, 3)}
+    dom = max(per_op, key=lambda k: per_op[k]["ms"])
+    d = per_op[dom]
+    roof = {"bound": "hbm", "kernel": d["kernel"], "achieved": d["GB/s"], "peak": hbm,
+            "unit": "GB/s", "frac": round(d["GB/s"] / hbm, 4),
+            "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+            "traffic": kernel_traffic(d["kernel"]),
+            "algorithmic_bytes_per_launch": d["algorithmic_bytes"]}
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic (counter-based SplitMix64, generated on the GPU)",
+        "config": {"workload": "8192x8192 int64 Poisson(5) count matrices A, B; x 8192 signed "
+                               "8-bit; step = pack A,B,x + unpack A + get 2^20 + A+B + 7A + Ax",
+                   "rows": N_ROWS, "cols": N_COLS, "seeds": list(wl.seeds),
+                   "widths": {k: v[0] for k, v in widths.items()},
+                   "l2": "inputs larger than L2 (dense A, B 512 MiB each, re-read every step)",
+                   "parallelism": f"replicas x{world} (independent problems)"},
+        "step_bytes": int(step_bytes), "per_op": per_op,
+        "matvec_GBps": per_op.get("matvec", {}).get("GB/s"),
+        "eta1_vs_int64": round((64 - widths["A"][0]) / 64, 4),
+        "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+    }
+    return line
+
+
+def run_e2e(wl, torch, args, barrier, dist, dev, world, step_bytes):
+    """Same step through the public API with host buffers: pinned host -> device
+    copies of the dense inputs, the step, and device -> host copies of every
+    result (unpacked A, the gathered entries, packed C, D and y)."""
+    hA = torch.empty_like(wl.A, device="cpu").pin_memory()
+    hB = torch.empty_like(wl.B, device="cpu").pin_memory()
+    hX = torch.empty_like(wl.X, device="cpu").pin_memory()
+    hA.copy_(wl.A)
+    hB.copy_(wl.B)
+    hX.copy_(wl.X)
+    dA, dB, dX = torch.empty_like(wl.A), torch.empty_like(wl.B), torch.empty_like(wl.X)
+    outs = [wl.unp, wl.got, wl.pc.buf, wl.pd.buf, wl.py.buf]
+    houts = [torch.empty_like(o, device="cpu").pin_memory() for o in outs]
+    h2d = hA.numel() * 8 + hB.numel() * 8 + hX.numel() * 8
+    d2h = sum(o.numel() * o.element_size() for o in outs)
+
+    def one():
+        dA.copy_(hA, non_blocking=True)
+        dB.copy_(hB, non_blocking=True)
+        dX.copy_(hX, non_blocking=True)
+        wl.step(A=dA, B=dB, X=dX)
+        for h, o in zip(houts, outs):
+            h.copy_(o, non_blocking=True)
+
+    steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        one()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    barrier()
+    sec = (time.perf_counter() - t0) / steps
+    if dist is not None:
+        t = torch.tensor([sec], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        sec = float(t.item())
+    assert torch.equal(houts[0], hA), "e2e unpack mismatch"
+    return {"value": round(world * step_bytes / sec / 1e9, 2), "unit": "GB/s",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": round(sec * 1e3, 4), "steps": steps,
+            "timing": "host wall clock around the copies and the step, synchronised"}
+
+
+# ---------------------------------------------------------------------------
+# the oracle, timed on the host cores
+# ---------------------------------------------------------------------------
+def oracle_sample(rows: int):
+    """Rows 0..rows-1 of the same workload, through the oracle (one thread)."""
+    import oracle
+    import synth
+    a = synth.count_matrix(SEED_A, synth.STREAM_A, rows, N_COLS, LAMBDA)
+    b = synth.count_matrix(SEED_B, synth.STREAM_B, rows, N_COLS, LAMBDA)
+    x = synth.uniform_int(SEED_A, synth.STREAM_X, N_COLS, -128, 127).reshape(-1, 1)
+    idx = synth.uniform_int(SEED_A, synth.STREAM_INDEX, max(1, GET_COUNT * rows // N_ROWS), 0,
+                            rows * N_COLS - 1)
+    t0 = time.perf_counter()
+    pa, pb, px = oracle.pack(a), oracle.pack(b), oracle.pack(x)
+    ua = oracle.unpack(pa)
+    g = oracle.get_flat(pa, idx[: min(idx.size, 4096)])
+    pc = oracle.add(pa, pb)
+    pd = oracle.scale(pa, SCALE)
+    py = oracle.matvec(pa, px)
+    sec = time.perf_counter() - t0
+    n = rows * N_COLS
+    bA, bB, bC, bD = pa.width, pb.width, pc.width, pd.width
+    nbytes = (2 * 8 * n + n * (bA + bB) / 8 + 8 * N_COLS + (n * bA / 8 + 8 * n)
+              + min(idx.size, 4096) * 20 + n * (bA + bB + bC) / 8 + n * (bA + bD) / 8
+              + n * bA / 8 + N_COLS + rows * py.width / 8)
+    assert np.array_equal(ua, a) and g.size > 0
+    return sec, nbytes
+
+
+def cpu_baseline(target_s: float = 12.0):
+    sec, nb = oracle_sample(64)
+    rows = int(min(N_ROWS, max(64, 64 * target_s / max(sec, 1e-3))))
+    rows = max(64, rows // 64 * 64)
+    sec, nb = oracle_sample(rows)
+    return {"value": round(nb / sec / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"rows 0..{rows - 1} of the 8192x8192 workload ({rows * N_COLS} entries): "
+                      f"pack A,B,x, unpack A, get 4096, A+B, 7A, Ax; {sec:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    rows = 128
+    for _ in range(args.warmup):
+        oracle_sample(rows)
+    secs, nbs = [], []
+    for _ in range(args.steps):
+        s, nb = oracle_sample(rows)
+        secs.append(s)
+        nbs.append(nb)
+    sec = sum(secs) / len(secs)
+    value = statistics.mean(nbs) / sec / 1e9
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(sec * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic (same generator)",
+        "config": {"workload": "8192x8192 int64 Poisson(5) count matrices A, B; x 8192 signed "
+                               "8-bit; step = pack A,B,x + unpack A + get + A+B + 7A + Ax",
+                   "sample_rows": rows},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"rows 0..{rows - 1} of the workload per step"},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ccm", choices=["ccm", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    line = run_gpu(args, rank, world, local_rank)
+    if line is not None:
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

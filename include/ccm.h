@@ -1,0 +1,223 @@
+/*
+ * ccm.h -- C ABI of libccm: computable compressed matrices on one GPU.
+ *
+ * A matrix of integers is stored in the paper's "Supreme Minimum" (SM) form
+ * (Methods, "Method 1: The Supreme Minimum"): every entry takes the same
+ * number of bits b, the smallest that holds every entry (Eq. 1), and the
+ * entries, unravelled row-major, are laid end to end in one LSB-first bit
+ * stream -- entry e owns bits [e*b, (e+1)*b) -- cut into 32-bit little-endian
+ * words (Eq. 3 and the step-by-step example after it: fields fill each word
+ * from its least significant bit upward, and a field that does not fit in the
+ * rest of a word straddles into the next one, low bits first).  32-bit little-endian words
+ * are byte-for-byte the paper's 64-bit bitstrings.
+ *
+ * Sign: the paper only treats non-negative entries (Methods, Matrix
+ * compression).  This library reads Eq. 1 as follows.  When no entry is
+ * negative the fields are unsigned and b = max(1, bitlen(max)), exactly
+ * Eq. 1.  Otherwise the fields are two's complement and
+ * b = 1 + max over entries of bitlen(a >= 0 ? a : -a - 1), the smallest b
+ * whose range [-2^(b-1), 2^(b-1)-1] holds every entry.  Widths run 1..64.
+ *
+ * Word count: ceil(rows*cols*b/32) data words, zero padded to a multiple of 4
+ * words (16 bytes); bits above the last field and the pad words are zero, so
+ * a packed matrix has exactly one representation.
+ *
+ * Operations on the compressed form (add, scale, matvec, matmul) compute the
+ * same integers as the operation on the uncompressed matrices (Introduction:
+ * the compressed form is meant to support the same mathematics as the
+ * original), exactly, and re-pack the result at its own new width by the rule
+ * above.
+ *
+ * Conventions for every entry point:
+ *  - All data pointers are DEVICE pointers on the current CUDA device and are
+ *    owned by the caller (the library never frees them).  `ccm_matrix` and
+ *    `ccm_header` pointers passed as arguments are HOST pointers to small
+ *    structs that carry those device pointers.
+ *  - Calls are asynchronous on `stream` (NULL = the legacy default stream)
+ *    unless documented as synchronous.
+ *  - Host-detectable errors (NULL pointers, bad dtype, shape mismatch,
+ *    too-small capacity or workspace) return a negative ccm_status at once and
+ *    launch nothing.
+ *  - Data-dependent errors (int64 overflow of a result, a result whose width
+ *    needs more words than the output capacity, an input header that is not a
+ *    valid matrix) are written by the GPU into the output header's `status`;
+ *    the output words are then left unwritten.  An input whose header carries
+ *    an error passes that error on to the output, so a chain of calls needs no
+ *    host synchronisation and still reports the first failure.
+ *  - No call traps, asserts or spins on the GPU.
+ */
+#ifndef CCM_H
+#define CCM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st* ccm_stream_t; /* the same handle as cudaStream_t */
+
+typedef enum ccm_status {
+  CCM_OK = 0,
+  CCM_E_INVAL = -1,    /* NULL pointer, bad dtype/path/op code */
+  CCM_E_SHAPE = -2,    /* operand shapes do not agree */
+  CCM_E_WIDTH = -3,    /* a width outside 1..64, or int32 output for a field that needs more */
+  CCM_E_OVERFLOW = -4, /* an exact result does not fit int64 */
+  CCM_E_CAPACITY = -5, /* output words or workspace too small */
+  CCM_E_RANGE = -6,    /* element index out of range */
+  CCM_E_CUDA = -7,     /* a CUDA runtime call failed */
+  CCM_E_TIMEOUT = -8,  /* a bounded device wait gave up */
+  CCM_E_INPUT = -9     /* an input header is not a valid packed matrix */
+} ccm_status;
+
+typedef enum ccm_dtype { CCM_I32 = 0, CCM_I64 = 1 } ccm_dtype;
+
+#define CCM_MAGIC 0x314D4343u /* "CCM1" */
+#define CCM_HEADER_BYTES 64
+
+/* Device-resident header of a packed matrix (64 bytes, 16-byte aligned).
+ * Written by the library; callers read it with ccm_header_read(). */
+typedef struct ccm_header {
+  uint32_t magic;     /* CCM_MAGIC once a call has produced the matrix */
+  int32_t width;      /* b, 1..64 */
+  int32_t is_signed;  /* 0: unsigned fields (Eq. 1); 1: two's complement */
+  int32_t status;     /* CCM_OK or the data-dependent error of the producing call */
+  uint64_t rows;
+  uint64_t cols;
+  uint64_t nwords;    /* ccm_words_for(rows, cols, width) */
+  uint64_t stat_or;   /* internal: OR over the result of (a >= 0 ? a : ~a) */
+  uint32_t stat_neg;  /* internal: 1 when some entry of the result is negative */
+  uint32_t reserved0;
+  uint64_t reserved1;
+} ccm_header;
+
+/* Host-side handle of one packed matrix: where it lives and its shape.
+ * `hdr` and `words` are device pointers; `capacity` counts the uint32 words
+ * available at `words`.  `rows`/`cols` are the shape the caller expects; the
+ * library checks them against each other on the host and against the header
+ * on the GPU. */
+typedef struct ccm_matrix {
+  ccm_header* hdr;
+  uint32_t* words;
+  uint64_t capacity;
+  uint64_t rows;
+  uint64_t cols;
+} ccm_matrix;
+
+/* Operation codes for ccm_workspace_bytes. */
+typedef enum ccm_op { CCM_OP_MATVEC = 1, CCM_OP_MATMUL = 2 } ccm_op;
+
+/* Matmul paths. */
+typedef enum ccm_matmul_path {
+  CCM_MATMUL_AUTO = 0,
+  CCM_MATMUL_TENSOR = 1,  /* exact 4-bit limb decomposition on the tcgen05 tensor cores */
+  CCM_MATMUL_CUDACORE = 2 /* decode-and-multiply on the integer ALUs */
+} ccm_matmul_path;
+
+/* Words needed for rows*cols fields of `width` bits: ceil(n*width/32) rounded
+ * up to a multiple of 4 (Methods, Method 1: the paper's bitstring count,
+ * restated for 32-bit words and 16-byte padding).  0 for an empty matrix or a
+ * width outside 1..64. */
+uint64_t ccm_words_for(uint64_t rows, uint64_t cols, int width);
+
+/* Human-readable name of a status code (static storage). */
+const char* ccm_status_str(int status);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int ccm_version(void);
+
+/* Width selection only (Eq. 1 with the signed reading): scans rows*cols
+ * dense entries (`dtype` CCM_I32 or CCM_I64, row-major, device) and writes
+ * width, is_signed, nwords, rows, cols and status into `hdr` (device).
+ * Lets a caller size the output exactly before ccm_pack. */
+ccm_status ccm_measure(const void* dense, int dtype, uint64_t rows, uint64_t cols,
+                       ccm_header* hdr, ccm_stream_t stream);
+
+/* SM compression (Methods, Method 1; Eq. 1 and Eq. 3): width selection over
+ * the dense matrix, then every entry written as a b-bit field at bit e*b of
+ * the stream.  `dense` is rows*cols entries of `dtype`, row-major, device.
+ * Output in `out` (header + words).  If the exact width needs more than
+ * out->capacity words the header gets CCM_E_CAPACITY and no words. */
+ccm_status ccm_pack(const void* dense, int dtype, uint64_t rows, uint64_t cols,
+                    const ccm_matrix* out, ccm_stream_t stream);
+
+/* Decompression: every field read back and sign- or zero-extended to
+ * `dtype`, row-major into `dense` (rows*cols entries, device).  CCM_I32
+ * output needs signed b <= 32 or unsigned b <= 31; otherwise CCM_E_WIDTH is
+ * written to `*err` (device int32, may be NULL) and `dense` is untouched.
+ * `*err` is set to CCM_OK on success when given. */
+ccm_status ccm_unpack(const ccm_matrix* a, void* dense, int dtype, int32_t* err,
+                      ccm_stream_t stream);
+
+/* Element access by row and column (Methods, Matrix compression: access to
+ * any element given its row i and column j).  `idx` holds `count` flat
+ * row-major indices i*cols + j (device uint64); `out` receives `count` int64
+ * entries (device).  An index >= rows*cols yields 0 and CCM_E_RANGE in
+ * `*err` (device int32, may be NULL). */
+ccm_status ccm_get(const ccm_matrix* a, const uint64_t* idx, uint64_t count, int64_t* out,
+                   int32_t* err, ccm_stream_t stream);
+
+/* C = A + B, exact, entrywise; A, B and C have the same shape; A and B may
+ * have different widths and sign modes.  C is re-packed at its own width. */
+ccm_status ccm_add(const ccm_matrix* a, const ccm_matrix* b, const ccm_matrix* c,
+                   ccm_stream_t stream);
+
+/* C = s * A for an int64 scalar s, exact; CCM_E_OVERFLOW when an entry does
+ * not fit int64.  C is re-packed at its own width. */
+ccm_status ccm_scale(const ccm_matrix* a, int64_t s, const ccm_matrix* c, ccm_stream_t stream);
+
+/* y = A x: A is m x n, x is a packed n x 1 matrix, y a packed m x 1 matrix,
+ * y_i = sum_j a_ij x_j exactly (CCM_E_OVERFLOW when y_i does not fit int64).
+ * `ws` is device workspace of at least ccm_workspace_bytes(CCM_OP_MATVEC,
+ * m, n, 1) bytes, 256-byte aligned; its contents need no initialisation. */
+ccm_status ccm_matvec(const ccm_matrix* a, const ccm_matrix* x, const ccm_matrix* y, void* ws,
+                      size_t ws_bytes, ccm_stream_t stream);
+
+/* C = A B: A is m x k, B is k x n, C is m x n, exact int64 entries
+ * (CCM_E_OVERFLOW otherwise), re-packed at C's own width.  `path` selects the
+ * tensor-core limb path or the CUDA-core path (AUTO = tensor when the inputs
+ * allow it).  `ws` as for ccm_matvec with CCM_OP_MATMUL and (m, k, n). */
+ccm_status ccm_matmul(const ccm_matrix* a, const ccm_matrix* b, const ccm_matrix* c, int path,
+                      void* ws, size_t ws_bytes, ccm_stream_t stream);
+
+/* Device workspace needed by `op` on an m x k by k x n problem (matvec: n = 1
+ * is the vector, k the inner size). */
+size_t ccm_workspace_bytes(int op, uint64_t m, uint64_t k, uint64_t n);
+
+/* Synchronous copy of a device header to host memory (waits for `stream`). */
+ccm_status ccm_header_read(const ccm_header* dev, ccm_header* host, ccm_stream_t stream);
+
+/* Synthetic inputs, generated on the GPU by the counter-based SplitMix64
+ * scheme of the test-input generator: entry i of stream `stream_id` under
+ * `seed` is mix(key + (i + 1) * 0x9E3779B97F4A7C15) with
+ * key = mix(seed + (stream_id + 1) * 0x9E3779B97F4A7C15) and mix the
+ * SplitMix64 finaliser (Steele, Lea and Flood 2014).  `start` offsets i.
+ * ccm_gen_uniform: int64 in [lo, hi] by the multiply-high map.
+ * ccm_gen_poisson: inversion of `table` (float64 CDF, `table_len` entries,
+ * device) on u = (draw >> 11) * 2^-53: the count of entries <= u. */
+ccm_status ccm_gen_uniform(int64_t* out, uint64_t count, uint64_t seed, uint64_t stream_id,
+                           uint64_t start, int64_t lo, int64_t hi, ccm_stream_t stream);
+ccm_status ccm_gen_poisson(int64_t* out, uint64_t count, uint64_t seed, uint64_t stream_id,
+                           uint64_t start, const double* table, uint32_t table_len,
+                           ccm_stream_t stream);
+
+/* Runtime instrumentation (no counterpart in the paper).
+ * ccm_launch_count: number of kernels this library has launched in this
+ * process so far (all devices, all threads).
+ * ccm_profile_next: brackets the main kernel of the NEXT ccm_* call made by
+ * the calling host thread with cudaEventRecord(start) before it and
+ * cudaEventRecord(stop) after it, on that call's stream, so the caller can
+ * time that one kernel with cudaEventElapsedTime.  `start` and `stop` are
+ * cudaEvent_t handles owned by the caller; NULL, NULL cancels.  The main
+ * kernel is: k_pack for ccm_pack/ccm_add/ccm_scale, k_stats for ccm_measure,
+ * k_unpack, k_get, and the product kernel of ccm_matvec/ccm_matmul. */
+uint64_t ccm_launch_count(void);
+ccm_status ccm_profile_next(void* start_event, void* stop_event);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCM_H */

@@ -19,16 +19,17 @@
  *    rule is exactly Eq. 1;
  *  - SM layout (Methods, "Method 1: The Supreme Minimum", Eq. 3 and the
  *    step-by-step example after it): the matrix is unravelled row-major and
- *    entry e occupies bits [e*b, (e+1)*b) of one LSB-first bit stream ("read
- *    from right to left"); a field that does not fit in what is left of a word
- *    straddles into the next one, low bits first.  The stream is cut into
+ *    entry e occupies bits [e*b, (e+1)*b) of one LSB-first bit stream (the
+ *    paper fills each bitstring from its least significant end); a field that
+ *    does not fit in what is left of a word straddles into the next one, low
+ *    bits first.  The stream is cut into
  *    32-bit little-endian words, which is byte-for-byte the paper's 64-bit
  *    bitstrings on a little-endian machine;
  *  - the word count: ceil(n*b/32) data words, zero-padded to a multiple of 4
  *    words (the paper's floor(n*b/64)+1 over-allocates when 64 divides n*b);
  *  - operations on the compressed form are defined as the same operation on
- *    the uncompressed integers (Introduction: compressed matrices undergo the
- *    same mathematical operations as the originals), carried out here on
+ *    the uncompressed integers (Introduction: the compressed form is meant to
+ *    support the same mathematics as the original), carried out here on
  *    unpacked int64 with 128-bit accumulation and an explicit int64 overflow
  *    check.  The result is re-packed with the width rule above.
  */

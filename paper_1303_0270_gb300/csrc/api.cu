@@ -1,0 +1,178 @@
+// api.cu -- the extern "C" entry points of libccm (declared in ccm.h): host
+// checks that need no GPU, then the launchers in pack.cu, matvec.cu and
+// matmul.cu.  Every entry point returns before launching anything when a
+// host-side check fails.
+#include <cuda_runtime.h>
+
+#include "ccm.h"
+#include "ccm_device.cuh"
+#include "kernels.h"
+
+namespace {
+
+using ccm::words_for;
+
+cudaStream_t to_cuda(ccm_stream_t s) { return reinterpret_cast<cudaStream_t>(s); }
+
+bool valid_out(const ccm_matrix* m) {
+  if (!m || !m->hdr) return false;
+  if (m->capacity && !m->words) return false;
+  if (reinterpret_cast<uintptr_t>(m->hdr) % 16 || reinterpret_cast<uintptr_t>(m->words) % 16)
+    return false;
+  return true;
+}
+
+bool valid_in(const ccm_matrix* m) {
+  if (!m || !m->hdr) return false;
+  if (m->rows * m->cols && !m->words) return false;
+  return reinterpret_cast<uintptr_t>(m->hdr) % 16 == 0;
+}
+
+ccm_status launched() {
+  return cudaGetLastError() == cudaSuccess ? CCM_OK : CCM_E_CUDA;
+}
+
+// Words a result can never go below (width 1); a smaller capacity is a
+// host-detectable error.
+bool capacity_ok(const ccm_matrix* m) { return m->capacity >= words_for(m->rows * m->cols, 1); }
+
+}  // namespace
+
+extern "C" {
+
+uint64_t ccm_words_for(uint64_t rows, uint64_t cols, int width) {
+  return words_for(rows * cols, width);
+}
+
+const char* ccm_status_str(int status) {
+  switch (status) {
+    case CCM_OK: return "CCM_OK";
+    case CCM_E_INVAL: return "CCM_E_INVAL";
+    case CCM_E_SHAPE: return "CCM_E_SHAPE";
+    case CCM_E_WIDTH: return "CCM_E_WIDTH";
+    case CCM_E_OVERFLOW: return "CCM_E_OVERFLOW";
+    case CCM_E_CAPACITY: return "CCM_E_CAPACITY";
+    case CCM_E_RANGE: return "CCM_E_RANGE";
+    case CCM_E_CUDA: return "CCM_E_CUDA";
+    case CCM_E_TIMEOUT: return "CCM_E_TIMEOUT";
+    case CCM_E_INPUT: return "CCM_E_INPUT";
+    default: return "CCM_E_UNKNOWN";
+  }
+}
+
+int ccm_version(void) { return 100; }
+
+ccm_status ccm_measure(const void* dense, int dtype, uint64_t rows, uint64_t cols,
+                       ccm_header* hdr, ccm_stream_t stream) {
+  if (!hdr || (rows * cols && !dense)) return CCM_E_INVAL;
+  if (dtype != CCM_I32 && dtype != CCM_I64) return CCM_E_INVAL;
+  ccm::run_measure(dense, dtype, rows, cols, hdr, to_cuda(stream));
+  return launched();
+}
+
+ccm_status ccm_pack(const void* dense, int dtype, uint64_t rows, uint64_t cols,
+                    const ccm_matrix* out, ccm_stream_t stream) {
+  if (!valid_out(out) || (rows * cols && !dense)) return CCM_E_INVAL;
+  if (dtype != CCM_I32 && dtype != CCM_I64) return CCM_E_INVAL;
+  if (out->rows != rows || out->cols != cols) return CCM_E_SHAPE;
+  if (!capacity_ok(out)) return CCM_E_CAPACITY;
+  ccm::run_pack(dense, dtype, rows, cols, *out, to_cuda(stream));
+  return launched();
+}
+
+ccm_status ccm_unpack(const ccm_matrix* a, void* dense, int dtype, int32_t* err,
+                      ccm_stream_t stream) {
+  if (!valid_in(a) || (a->rows * a->cols && !dense)) return CCM_E_INVAL;
+  if (dtype != CCM_I32 && dtype != CCM_I64) return CCM_E_INVAL;
+  if (a->rows * a->cols == 0 && !err) return CCM_OK;
+  ccm::run_unpack(*a, dense, dtype, err, to_cuda(stream));
+  return launched();
+}
+
+ccm_status ccm_get(const ccm_matrix* a, const uint64_t* idx, uint64_t count, int64_t* out,
+                   int32_t* err, ccm_stream_t stream) {
+  if (!valid_in(a) || (count && (!idx || !out))) return CCM_E_INVAL;
+  ccm::run_get(*a, idx, count, out, err, to_cuda(stream));
+  return launched();
+}
+
+ccm_status ccm_add(const ccm_matrix* a, const ccm_matrix* b, const ccm_matrix* c,
+                   ccm_stream_t stream) {
+  if (!valid_in(a) || !valid_in(b) || !valid_out(c)) return CCM_E_INVAL;
+  if (a->rows != b->rows || a->cols != b->cols || c->rows != a->rows || c->cols != a->cols)
+    return CCM_E_SHAPE;
+  if (!capacity_ok(c)) return CCM_E_CAPACITY;
+  ccm::run_add(*a, *b, *c, to_cuda(stream));
+  return launched();
+}
+
+ccm_status ccm_scale(const ccm_matrix* a, int64_t s, const ccm_matrix* c, ccm_stream_t stream) {
+  if (!valid_in(a) || !valid_out(c)) return CCM_E_INVAL;
+  if (c->rows != a->rows || c->cols != a->cols) return CCM_E_SHAPE;
+  if (!capacity_ok(c)) return CCM_E_CAPACITY;
+  ccm::run_scale(*a, s, *c, to_cuda(stream));
+  return launched();
+}
+
+size_t ccm_workspace_bytes(int op, uint64_t m, uint64_t k, uint64_t n) {
+  switch (op) {
+    case CCM_OP_MATVEC: return ccm::matvec_workspace(m, k);
+    case CCM_OP_MATMUL: return ccm::matmul_workspace(m, k, n);
+    default: return 0;
+  }
+}
+
+ccm_status ccm_matvec(const ccm_matrix* a, const ccm_matrix* x, const ccm_matrix* y, void* ws,
+                      size_t ws_bytes, ccm_stream_t stream) {
+  if (!valid_in(a) || !valid_in(x) || !valid_out(y) || !ws) return CCM_E_INVAL;
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return CCM_E_INVAL;
+  if (x->rows != a->cols || x->cols != 1 || y->rows != a->rows || y->cols != 1)
+    return CCM_E_SHAPE;
+  if (!capacity_ok(y)) return CCM_E_CAPACITY;
+  if (ws_bytes < ccm::matvec_workspace(a->rows, a->cols)) return CCM_E_CAPACITY;
+  ccm::run_matvec(*a, *x, *y, ws, to_cuda(stream));
+  return launched();
+}
+
+ccm_status ccm_matmul(const ccm_matrix* a, const ccm_matrix* b, const ccm_matrix* c, int path,
+                      void* ws, size_t ws_bytes, ccm_stream_t stream) {
+  if (!valid_in(a) || !valid_in(b) || !valid_out(c) || !ws) return CCM_E_INVAL;
+  if (path != CCM_MATMUL_AUTO && path != CCM_MATMUL_TENSOR && path != CCM_MATMUL_CUDACORE)
+    return CCM_E_INVAL;
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return CCM_E_INVAL;
+  if (b->rows != a->cols || c->rows != a->rows || c->cols != b->cols) return CCM_E_SHAPE;
+  if (!capacity_ok(c)) return CCM_E_CAPACITY;
+  if (ws_bytes < ccm::matmul_workspace(a->rows, a->cols, b->cols)) return CCM_E_CAPACITY;
+  int st = ccm::run_matmul(*a, *b, *c, path, ws, to_cuda(stream));
+  if (st != CCM_OK) return (ccm_status)st;
+  return launched();
+}
+
+ccm_status ccm_header_read(const ccm_header* dev, ccm_header* host, ccm_stream_t stream) {
+  if (!dev || !host) return CCM_E_INVAL;
+  cudaStream_t s = to_cuda(stream);
+  if (cudaMemcpyAsync(host, dev, sizeof(ccm_header), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return CCM_E_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return CCM_E_CUDA;
+  return CCM_OK;
+}
+
+ccm_status ccm_gen_uniform(int64_t* out, uint64_t count, uint64_t seed, uint64_t stream_id,
+                           uint64_t start, int64_t lo, int64_t hi, ccm_stream_t stream) {
+  if (count && !out) return CCM_E_INVAL;
+  if (hi < lo) return CCM_E_INVAL;
+  if (!count) return CCM_OK;
+  ccm::run_gen_uniform(out, count, seed, stream_id, start, lo, hi, to_cuda(stream));
+  return launched();
+}
+
+ccm_status ccm_gen_poisson(int64_t* out, uint64_t count, uint64_t seed, uint64_t stream_id,
+                           uint64_t start, const double* table, uint32_t table_len,
+                           ccm_stream_t stream) {
+  if ((count && !out) || !table || table_len == 0 || table_len > 4096) return CCM_E_INVAL;
+  if (!count) return CCM_OK;
+  ccm::run_gen_poisson(out, count, seed, stream_id, start, table, table_len, to_cuda(stream));
+  return launched();
+}
+
+}  // extern "C"

@@ -1,0 +1,41 @@
+// kernels.h -- host-side launchers behind the C ABI (internal to libccm).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ccm.h"
+
+namespace ccm {
+
+int num_sms();
+
+// Launch accounting and the per-call profiling hook (ccm_profile_next).
+void note_launch(int count = 1);
+void profile_begin(cudaStream_t st);
+void profile_end(cudaStream_t st);
+
+void run_measure(const void* dense, int dtype, uint64_t rows, uint64_t cols, ccm_header* hdr,
+                 cudaStream_t st);
+void run_pack(const void* dense, int dtype, uint64_t rows, uint64_t cols, const ccm_matrix& out,
+              cudaStream_t st);
+void run_unpack(const ccm_matrix& a, void* dense, int dtype, int32_t* err, cudaStream_t st);
+void run_get(const ccm_matrix& a, const uint64_t* idx, uint64_t count, int64_t* out, int32_t* err,
+             cudaStream_t st);
+void run_add(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, cudaStream_t st);
+void run_scale(const ccm_matrix& a, int64_t s, const ccm_matrix& c, cudaStream_t st);
+void run_pack_scratch(const int64_t* vals, const ccm_matrix& out, cudaStream_t st);
+
+size_t matvec_workspace(uint64_t m, uint64_t n);
+void run_matvec(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& y, void* ws,
+                cudaStream_t st);
+
+size_t matmul_workspace(uint64_t m, uint64_t k, uint64_t n);
+int run_matmul(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, int path, void* ws,
+               cudaStream_t st);
+
+void run_gen_uniform(int64_t* out, uint64_t count, uint64_t seed, uint64_t stream_id,
+                     uint64_t start, int64_t lo, int64_t hi, cudaStream_t st);
+void run_gen_poisson(int64_t* out, uint64_t count, uint64_t seed, uint64_t stream_id,
+                     uint64_t start, const double* table, uint32_t table_len, cudaStream_t st);
+
+}  // namespace ccm

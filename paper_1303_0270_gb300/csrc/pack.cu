@@ -1,0 +1,239 @@
+// pack.cu -- SM compression and decompression kernels (Methods, Method 1):
+// width selection + pack of dense int32/int64 matrices, unpack, element
+// access, and the elementwise operations whose results are re-packed by the
+// same engine (add, scale).
+#include "pack_engine.cuh"
+#include "kernels.h"
+
+namespace ccm {
+
+int num_sms() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  static int cached_dev = -1, cached = 0;
+  if (dev != cached_dev) {
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cached = sms > 0 ? sms : 1;
+    cached_dev = dev;
+  }
+  return cached;
+}
+
+__global__ void k_init(InitArgs a) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int st = CCM_OK;
+    if (a.in0) st = check_input(a.in0, a.in0_rows, a.in0_cols, a.in0_capacity);
+    if (st == CCM_OK && a.in1) st = check_input(a.in1, a.in1_rows, a.in1_cols, a.in1_capacity);
+    ccm_header* o = a.out;
+    o->magic = CCM_MAGIC;
+    o->width = 0;
+    o->is_signed = 0;
+    o->status = st;
+    o->rows = a.out_rows;
+    o->cols = a.out_cols;
+    o->nwords = 0;
+    o->stat_or = 0;
+    o->stat_neg = 0;
+    o->reserved0 = 0;
+    o->reserved1 = 0;
+  }
+  if (a.zero_ptr) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.zero_count; i += stride)
+      a.zero_ptr[i] = 0;
+  }
+}
+
+void launch_init(const InitArgs& a, cudaStream_t st) {
+  int grid = 1;
+  if (a.zero_ptr && a.zero_count > 256)
+    grid = (int)umin((a.zero_count + 255) / 256, (uint64_t)num_sms() * 4);
+  k_init<<<grid, 256, 0, st>>>(a);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// pack / measure
+// ---------------------------------------------------------------------------
+// Finalises the header of a measure-only call (no words): width, sign, nwords.
+__global__ void k_measure_finish(ccm_header* out, uint64_t n) {
+  if (out->status != CCM_OK) return;
+  int b = width_from_stats(out->stat_or, out->stat_neg);
+  out->width = b;
+  out->is_signed = out->stat_neg ? 1 : 0;
+  out->nwords = words_for(n, b);
+}
+
+void run_measure(const void* dense, int dtype, uint64_t rows, uint64_t cols, ccm_header* hdr,
+                 cudaStream_t st) {
+  InitArgs ia{};
+  ia.out = hdr;
+  ia.out_rows = rows;
+  ia.out_cols = cols;
+  launch_init(ia, st);
+  uint64_t n = rows * cols;
+  if (n) {
+    profile_begin(st);
+    if (dtype == CCM_I64)
+      launch_stats(ProdDenseI64{(const int64_t*)dense}, hdr, n, st);
+    else
+      launch_stats(ProdDenseI32{(const int32_t*)dense}, hdr, n, st);
+    profile_end(st);
+  }
+  k_measure_finish<<<1, 1, 0, st>>>(hdr, n);
+  note_launch();
+}
+
+void run_pack(const void* dense, int dtype, uint64_t rows, uint64_t cols, const ccm_matrix& out,
+              cudaStream_t st) {
+  InitArgs ia{};
+  ia.out = out.hdr;
+  ia.out_rows = rows;
+  ia.out_cols = cols;
+  launch_init(ia, st);
+  uint64_t n = rows * cols;
+  if (dtype == CCM_I64) {
+    ProdDenseI64 p{(const int64_t*)dense};
+    if (n) launch_stats(p, out.hdr, n, st);
+    profile_begin(st);
+    launch_pack(p, out.hdr, out.words, out.capacity, n, st);
+    profile_end(st);
+  } else {
+    ProdDenseI32 p{(const int32_t*)dense};
+    if (n) launch_stats(p, out.hdr, n, st);
+    profile_begin(st);
+    launch_pack(p, out.hdr, out.words, out.capacity, n, st);
+    profile_end(st);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// unpack: every field, sign/zero extended, to int64 or int32.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_unpack(const ccm_header* h, const uint32_t* __restrict__ w,
+                                                uint64_t rows, uint64_t cols, uint64_t capacity,
+                                                T* __restrict__ out, int32_t* err) {
+  int st = check_input(h, rows, cols, capacity);
+  const int b = h->width, sgn = h->is_signed;
+  if (st == CCM_OK && sizeof(T) == 4 && (sgn ? b > 32 : b > 31)) st = CCM_E_WIDTH;
+  if (st != CCM_OK) {
+    if (err && blockIdx.x == 0 && threadIdx.x == 0) *err = st;
+    return;
+  }
+  if (err && blockIdx.x == 0 && threadIdx.x == 0) *err = CCM_OK;
+  const uint64_t n = rows * cols;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    out[i] = (T)decode_field(w, i, b, sgn);
+}
+
+void run_unpack(const ccm_matrix& a, void* dense, int dtype, int32_t* err, cudaStream_t st) {
+  uint64_t n = a.rows * a.cols;
+  int grid = (int)umin(umax((n + 255) / 256, 1), (uint64_t)num_sms() * 16);
+  profile_begin(st);
+  if (dtype == CCM_I64)
+    k_unpack<int64_t><<<grid, 256, 0, st>>>(a.hdr, a.words, a.rows, a.cols, a.capacity,
+                                            (int64_t*)dense, err);
+  else
+    k_unpack<int32_t><<<grid, 256, 0, st>>>(a.hdr, a.words, a.rows, a.cols, a.capacity,
+                                            (int32_t*)dense, err);
+  profile_end(st);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// get: element access by flat row-major index.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_get(const ccm_header* h, const uint32_t* __restrict__ w,
+                                             uint64_t rows, uint64_t cols, uint64_t capacity,
+                                             const uint64_t* __restrict__ idx, uint64_t count,
+                                             int64_t* __restrict__ out, int32_t* err) {
+  int st = check_input(h, rows, cols, capacity);
+  if (err && blockIdx.x == 0 && threadIdx.x == 0 && st != CCM_OK) *err = st;
+  if (st != CCM_OK) return;
+  const int b = h->width, sgn = h->is_signed;
+  const uint64_t n = rows * cols;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  int bad = 0;
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += stride) {
+    uint64_t e = idx[k];
+    if (e < n) {
+      out[k] = decode_field(w, e, b, sgn);
+    } else {
+      out[k] = 0;
+      bad = 1;
+    }
+  }
+  if (err && bad) atomicCAS(err, CCM_OK, CCM_E_RANGE);
+}
+
+__global__ void k_set_i32(int32_t* p, int32_t v) { *p = v; }
+
+void run_get(const ccm_matrix& a, const uint64_t* idx, uint64_t count, int64_t* out, int32_t* err,
+             cudaStream_t st) {
+  if (err) {
+    k_set_i32<<<1, 1, 0, st>>>(err, CCM_OK);
+    note_launch();
+  }
+  if (!count) return;
+  int grid = (int)umin((count + 255) / 256, (uint64_t)num_sms() * 8);
+  profile_begin(st);
+  k_get<<<grid, 256, 0, st>>>(a.hdr, a.words, a.rows, a.cols, a.capacity, idx, count, out,
+                              err);
+  profile_end(st);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// add / scale
+// ---------------------------------------------------------------------------
+void run_add(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, cudaStream_t st) {
+  InitArgs ia{};
+  ia.out = c.hdr;
+  ia.in0 = a.hdr;
+  ia.in1 = b.hdr;
+  ia.in0_rows = a.rows;
+  ia.in0_cols = a.cols;
+  ia.in0_capacity = a.capacity;
+  ia.in1_rows = b.rows;
+  ia.in1_cols = b.cols;
+  ia.in1_capacity = b.capacity;
+  ia.out_rows = c.rows;
+  ia.out_cols = c.cols;
+  launch_init(ia, st);
+  ProdAdd p{{a.hdr, a.words, 0, 0}, {b.hdr, b.words, 0, 0}};
+  uint64_t n = c.rows * c.cols;
+  if (n) launch_stats(p, c.hdr, n, st);
+  profile_begin(st);
+  launch_pack(p, c.hdr, c.words, c.capacity, n, st);
+  profile_end(st);
+}
+
+void run_scale(const ccm_matrix& a, int64_t s, const ccm_matrix& c, cudaStream_t st) {
+  InitArgs ia{};
+  ia.out = c.hdr;
+  ia.in0 = a.hdr;
+  ia.in0_rows = a.rows;
+  ia.in0_cols = a.cols;
+  ia.in0_capacity = a.capacity;
+  ia.out_rows = c.rows;
+  ia.out_cols = c.cols;
+  launch_init(ia, st);
+  ProdScale p{{a.hdr, a.words, 0, 0}, s};
+  uint64_t n = c.rows * c.cols;
+  if (n) launch_stats(p, c.hdr, n, st);
+  profile_begin(st);
+  launch_pack(p, c.hdr, c.words, c.capacity, n, st);
+  profile_end(st);
+}
+
+// Pack an int64 result held in device scratch (matvec / matmul epilogue).
+void run_pack_scratch(const int64_t* vals, const ccm_matrix& out, cudaStream_t st) {
+  ProdDenseI64 p{vals};
+  uint64_t n = out.rows * out.cols;
+  if (n) launch_stats(p, out.hdr, n, st);
+  launch_pack(p, out.hdr, out.words, out.capacity, n, st);
+}
+
+}  // namespace ccm

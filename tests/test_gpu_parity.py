@@ -1,0 +1,231 @@
+"""GPU parity: every hot-path step through the C ABI against the oracle,
+word for word (integer work: tolerance 0), on seeded inputs that span several
+1024-field tiles with ragged tails, every width 1..64 in both sign modes, and
+the degenerate cases (empty, 1x1, all-zero, all-minus-one, exact word ends)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import assert_same_packed, device, lib_ccm, to_dev, torch, words_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ccm():
+    device()
+    return lib_ccm()
+
+
+def _rand(seed, shape, b, signed=True):
+    n = int(np.prod(shape))
+    if signed:
+        v = synth.uniform_signed(seed, 0, n, b)
+    else:
+        v = synth.uniform_int(seed, 0, n, 0, (1 << b) - 1 if b < 63 else (1 << 63) - 1)
+    v = v.reshape(shape)
+    if n:
+        lo, hi = synth.signed_range(b) if signed else (0, (1 << min(b, 63)) - 1)
+        v.flat[0] = lo
+        v.flat[-1] = hi
+    return v
+
+
+SHAPES = [(1, 1), (1, 31), (7, 13), (33, 65), (3, 1000), (5, 2048)]
+
+
+@pytest.mark.parametrize("b", list(range(1, 65)))
+@pytest.mark.parametrize("signed", [0, 1])
+def test_pack_unpack_every_width(ccm, b, signed):
+    if not signed and b == 64:
+        pytest.skip("int64 holds unsigned values up to 63 bits")
+    for shape in SHAPES:
+        a = _rand(b * 7 + signed, shape, b, bool(signed))
+        o = oracle.pack(a)
+        assert o.width == b
+        p = ccm.pack(to_dev(a))
+        assert_same_packed(p, o, f"pack b={b} s={signed} {shape}")
+        assert np.array_equal(ccm.unpack(p).cpu().numpy(), a)
+        if (signed and b <= 32) or (not signed and b <= 31):
+            assert np.array_equal(ccm.unpack(p, dtype=torch.int32).cpu().numpy(), a)
+        else:
+            with pytest.raises(ccm.CCMError):
+                ccm.unpack(p, dtype=torch.int32)
+
+
+def test_pack_int32_input_and_degenerate(ccm):
+    a, _, _, _ = synth.pr1_inputs()
+    p = ccm.pack(to_dev(a, np.int32))
+    assert_same_packed(p, oracle.pack(a), "pack int32 PR1")
+    assert p.width == 8 and p.is_signed == 1
+    for arr in (np.zeros((9, 70)), -np.ones((9, 70)), np.ones((1, 1)), np.zeros((1, 1))):
+        arr = arr.astype(np.int64)
+        assert_same_packed(ccm.pack(to_dev(arr)), oracle.pack(arr), "degenerate")
+    # fields that end exactly on word ends: 32 fields of width 4 -> 4 words
+    arr = np.arange(32, dtype=np.int64).reshape(4, 8) % 16
+    assert_same_packed(ccm.pack(to_dev(arr)), oracle.pack(arr), "word end")
+
+
+def test_empty_matrix(ccm):
+    dev = device()
+    p = ccm.pack(torch.empty((0, 5), dtype=torch.int64, device=dev))
+    h = p.header()
+    assert (h.status, h.width, h.nwords, h.rows, h.cols) == (0, 1, 0, 0, 5)
+    assert ccm.unpack(p).shape == (0, 5)
+
+
+def test_get(ccm):
+    a = _rand(11, (37, 91), 13)
+    p = ccm.pack(to_dev(a))
+    idx = synth.uniform_int(5, synth.STREAM_INDEX, 5000, 0, a.size - 1)
+    idx[:2] = [0, a.size - 1]
+    got = ccm.get(p, torch.from_numpy(idx)).cpu().numpy()
+    assert np.array_equal(got, a.ravel()[idx])
+    o = oracle.pack(a)
+    assert [oracle.get(o, int(e) // 91, int(e) % 91) for e in idx[:50]] == got[:50].tolist()
+    with pytest.raises(ccm.CCMError) as ei:
+        ccm.get(p, torch.tensor([3, a.size], dtype=torch.int64))
+    assert ei.value.status == ccm.E_RANGE
+
+
+@pytest.mark.parametrize("ba,bb,sa,sb", [(1, 1, 0, 0), (5, 5, 0, 0), (8, 8, 1, 1), (13, 3, 1, 0),
+                                         (32, 32, 1, 1), (33, 20, 1, 1), (62, 62, 1, 1),
+                                         (63, 63, 1, 1), (64, 10, 1, 1)])
+def test_add(ccm, ba, bb, sa, sb):
+    for shape in [(1, 1), (17, 33), (3, 1000)]:
+        a, b = _rand(ba, shape, ba, sa), _rand(bb + 100, shape, bb, sb)
+        if ba == 64:
+            b = np.where(a > 0, -np.abs(b), np.abs(b))  # keep the sum inside int64
+        o = oracle.add(oracle.pack(a), oracle.pack(b))
+        assert_same_packed(ccm.add(ccm.pack(to_dev(a)), ccm.pack(to_dev(b))), o,
+                           f"add {ba}/{bb} {shape}")
+
+
+def test_add_overflow_and_inverse(ccm):
+    a = np.array([[(1 << 63) - 1, 5]], dtype=np.int64)
+    b = np.array([[1, 5]], dtype=np.int64)
+    c = ccm.add(ccm.pack(to_dev(a)), ccm.pack(to_dev(b)), capacity=16)
+    assert c.status == ccm.E_OVERFLOW
+    x = _rand(3, (40, 50), 20)
+    z = ccm.add(ccm.pack(to_dev(x)), ccm.pack(to_dev(-x)))
+    assert (z.width, z.is_signed) == (1, 0) and not words_np(z).any()
+
+
+@pytest.mark.parametrize("s", [0, 1, -1, 7, -3, 1 << 20, -(1 << 30) + 5, (1 << 40) + 1])
+@pytest.mark.parametrize("b", [1, 5, 8, 20])
+def test_scale(ccm, s, b):
+    for shape in [(1, 1), (11, 6), (3, 1000)]:
+        a = _rand(b + 5, shape, b)
+        pa = ccm.pack(to_dev(a))
+        c = ccm.scale(pa, s)
+        assert_same_packed(c, oracle.scale(oracle.pack(a), s), f"scale {s} b={b}")
+        if s == 1:
+            assert np.array_equal(words_np(c), words_np(pa))
+
+
+def test_scale_overflow_and_capacity(ccm):
+    pa = ccm.pack(to_dev(np.array([[1 << 40, 3]])))
+    assert ccm.scale(pa, 1 << 23, capacity=16).status == ccm.E_OVERFLOW
+    c = ccm.scale(pa, 2, capacity=4)  # needs 42-bit fields: 3 words, padded to 4 -> fits
+    assert c.status == 0
+    big = ccm.pack(to_dev(_rand(1, (100, 100), 30)))
+    c = ccm.scale(big, 1 << 20, capacity=ccm.words_for(100, 100, 1))
+    assert c.status == ccm.E_CAPACITY
+
+
+def test_error_propagates_through_a_chain(ccm):
+    pa = ccm.pack(to_dev(np.array([[1 << 62, 1]])))
+    bad = ccm.scale(pa, 4, capacity=16)  # overflow
+    c = ccm.add(bad, pa, capacity=16)
+    assert c.status == ccm.E_OVERFLOW
+    d = ccm.scale(c, 1, capacity=16)
+    assert d.status == ccm.E_OVERFLOW
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (5, 3), (3, 5), (31, 33), (64, 130), (256, 256),
+                                 (100, 1000), (1000, 100)])
+@pytest.mark.parametrize("ba,bx", [(1, 1), (5, 8), (8, 8), (16, 8), (32, 8), (24, 24),
+                                   (40, 30)])
+def test_matvec(ccm, m, n, ba, bx):
+    a, x = _rand(m * 3 + ba, (m, n), ba), _rand(n + bx, (n, 1), bx)
+    oa, ox = oracle.pack(a), oracle.pack(x)
+    try:
+        o = oracle.matvec(oa, ox)
+    except OverflowError:
+        o = None
+    y = ccm.matvec(ccm.pack(to_dev(a)), ccm.pack(to_dev(x)), capacity=ccm.words_for(m, 1, 64))
+    if o is None:
+        assert y.status == ccm.E_OVERFLOW
+    else:
+        assert_same_packed(y, o, f"matvec {m}x{n} b={ba}/{bx}")
+
+
+def test_matvec_one_hot_and_empty_inner(ccm):
+    a = _rand(2, (13, 9), 10)
+    pa = ccm.pack(to_dev(a))
+    for j in (0, 4, 8):
+        x = np.zeros((9, 1), dtype=np.int64)
+        x[j] = 1
+        y = ccm.matvec(pa, ccm.pack(to_dev(x)))
+        assert np.array_equal(ccm.unpack(y).cpu().numpy().ravel(), a[:, j])
+    dev = device()
+    e = ccm.pack(torch.empty((4, 0), dtype=torch.int64, device=dev))
+    x0 = ccm.pack(torch.empty((0, 1), dtype=torch.int64, device=dev))
+    y = ccm.matvec(e, x0, capacity=4)
+    assert y.status == 0 and y.width == 1 and not ccm.unpack(y).any()
+
+
+def test_matvec_pr1(ccm):
+    a, _, x, _ = synth.pr1_inputs()
+    o = oracle.matvec(oracle.pack(a), oracle.pack(x.reshape(-1, 1)))
+    y = ccm.matvec(ccm.pack(to_dev(a, np.int32)), ccm.pack(to_dev(x.reshape(-1, 1), np.int32)))
+    assert_same_packed(y, o, "matvec PR1")
+
+
+@pytest.mark.parametrize("path", ["cuda", "auto"])
+@pytest.mark.parametrize("m,k,n", [(1, 1, 1), (2, 3, 4), (9, 17, 6), (33, 40, 31),
+                                   (64, 64, 64), (130, 70, 90)])
+@pytest.mark.parametrize("b", [1, 4, 8, 12, 16, 31])
+def test_matmul(ccm, path, m, k, n, b):
+    a, bm = _rand(m + k + b, (m, k), b), _rand(n + b, (k, n), b)
+    o = oracle.matmul(oracle.pack(a), oracle.pack(bm))
+    p = ccm.MATMUL_CUDACORE if path == "cuda" else ccm.MATMUL_AUTO
+    c = ccm.matmul(ccm.pack(to_dev(a)), ccm.pack(to_dev(bm)), path=p)
+    assert_same_packed(c, o, f"matmul {path} {m}x{k}x{n} b={b}")
+
+
+def test_matmul_identity_and_overflow(ccm):
+    a = _rand(4, (7, 7), 9)
+    eye = ccm.pack(to_dev(np.eye(7, dtype=np.int64)))
+    pa = ccm.pack(to_dev(a))
+    assert np.array_equal(ccm.unpack(ccm.matmul(eye, pa)).cpu().numpy(), a)
+    big = np.full((2, 3), 1 << 61, dtype=np.int64)
+    c = ccm.matmul(ccm.pack(to_dev(big)), ccm.pack(to_dev(big.T.copy())), capacity=16,
+                   path=ccm.MATMUL_CUDACORE)
+    assert c.status == ccm.E_OVERFLOW
+
+
+def test_pr1_full_chain(ccm):
+    """PR1: 256x256 int32 A, B in [-100, 100], x, s = 7 -- every op, bit-exact."""
+    a, b, x, s = synth.pr1_inputs()
+    oa, ob, ox = oracle.pack(a), oracle.pack(b), oracle.pack(x.reshape(-1, 1))
+    pa, pb = ccm.pack(to_dev(a, np.int32)), ccm.pack(to_dev(b, np.int32))
+    px = ccm.pack(to_dev(x.reshape(-1, 1), np.int32))
+    assert_same_packed(pa, oa, "PR1 pack A")
+    assert pa.width == 8
+    assert np.array_equal(ccm.unpack(pa, dtype=torch.int32).cpu().numpy(), a)
+    assert_same_packed(ccm.add(pa, pb), oracle.add(oa, ob), "PR1 add")
+    assert_same_packed(ccm.scale(pa, s), oracle.scale(oa, s), "PR1 scale")
+    assert_same_packed(ccm.matvec(pa, px), oracle.matvec(oa, ox), "PR1 matvec")
+    for path in (ccm.MATMUL_CUDACORE, ccm.MATMUL_AUTO):
+        assert_same_packed(ccm.matmul(pa, pb, path=path), oracle.matmul(oa, ob), "PR1 matmul")
+
+
+def test_device_generator_matches_synth(ccm):
+    for lo, hi in [(-100, 100), (-(1 << 31), (1 << 31) - 1), (0, 1), (-(1 << 63), (1 << 63) - 1)]:
+        g = ccm.gen_uniform(10000, 1303, 2, lo, hi, start=77).cpu().numpy()
+        assert np.array_equal(g, synth.uniform_int(1303, 2, 10000, lo, hi, start=77))
+    table = torch.from_numpy(synth.poisson_cdf_table(5.0))
+    g = ccm.gen_poisson(200000, 1303, 0, table).cpu().numpy()
+    assert np.array_equal(g, synth.poisson(1303, 0, 200000, 5.0))
