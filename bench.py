@@ -140,6 +140,16 @@ class Workload:
         self.profiled = ["pack", "unpack", "add", "scale", "matvec"]
         self.events = {k: [] for k in self.profiled}
 
+    def event_pair(self):
+        """Two timing events whose CUDA handles exist already (torch creates
+        an event lazily at its first record, so record each once here)."""
+        pair = []
+        for _ in range(2):
+            e = self.torch.cuda.Event(enable_timing=True)
+            e.record()
+            pair.append(e)
+        return pair
+
     def step(self, profile: bool = False, A=None, B=None, X=None):
         """One pass of the hot path through the C ABI (asynchronous)."""
         import ctypes
@@ -152,8 +162,7 @@ class Workload:
 
         def prof(name):
             if profile:
-                e0 = self.torch.cuda.Event(enable_timing=True)
-                e1 = self.torch.cuda.Event(enable_timing=True)
+                e0, e1 = self.event_pair()
                 ccm.profile_next(e0, e1)
                 self.events[name].append((e0, e1))
 

@@ -1,0 +1,11 @@
+// ew16.cu -- the group-engine elementwise kernels for widths <= 16 (see
+// ew_kernels.cuh); one translation unit per width class.
+#include "ew_kernels.cuh"
+
+namespace ccm {
+namespace ge {
+
+template void launch_ew_class<16>(const EwCall& c, cudaStream_t st);
+
+}  // namespace ge
+}  // namespace ccm

@@ -9,6 +9,11 @@ namespace ccm {
 
 int num_sms();
 
+// Largest width whose words fit `capacity` words for n fields (64 for n = 0):
+// a bound the host can compute although the width itself lives on the GPU.
+int width_bound(uint64_t capacity, uint64_t n);
+int bitlen_host(uint64_t v);
+
 // Launch accounting and the per-call profiling hook (ccm_profile_next).
 void note_launch(int count = 1);
 void profile_begin(cudaStream_t st);

@@ -5,12 +5,21 @@
 // at its own width by the pack engine.
 //
 // Launch sequence on the stream:
-//   k_init          validate A (m x n) and x (n x 1), clear y's header
-//   k_decode_vec    x -> int64 scratch (n entries)
-//   k_matvec_rows   one warp per row, fields decoded from A's words
+//   k_init          validate A (m x n) and x (n x 1), clear y's header and
+//                   the int64 y scratch
+//   k_matvec_fast   when cols % 128 == 0 and the buffers bound both widths
+//                   by 31/32 bits (see matvec_fast.cuh); otherwise
+//     k_decode_vec  x -> int64 scratch, and
+//     k_matvec_rows one warp per row, fields decoded from A's words
 //   k_stats, k_pack y scratch -> packed y
+//
+// The host cannot see the widths (they live in device headers), but a
+// buffer of `capacity` words can only hold a matrix of width
+// <= 32*capacity/(rows*cols); that bound picks the kernel and sizes its
+// shared memory.
 #include "pack_engine.cuh"
 #include "kernels.h"
+#include "matvec_fast.cuh"
 
 namespace ccm {
 
@@ -108,7 +117,37 @@ void run_matvec(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& y, v
     ia.zero_ptr = yv;
     ia.zero_count = m;
   }
+  const int bmax_a = width_bound(a.capacity, m * n), bmax_x = width_bound(x.capacity, n);
+  const bool fast = m && n && n % mvf::kKC == 0 && bmax_a <= 32 && bmax_x <= 31 &&
+                    bmax_a + bmax_x + bitlen_host(n) <= 63;
+  if (fast) ia.zero_ptr = yv, ia.zero_count = m;
   launch_init(ia, st);
+  if (fast) {
+    const int warps = bmax_a <= 12 ? 8 : 4;
+    const uint64_t row_blocks = (m + 32 * warps - 1) / (32 * warps);
+    const uint64_t groups = n / mvf::kKC;  // 128-column groups
+    const uint64_t target = (uint64_t)num_sms() * 8;
+    uint64_t splits = umin(umax((target + row_blocks - 1) / row_blocks, 1), groups);
+    splits = umin(splits, 65535);
+    const uint64_t per = (groups + splits - 1) / splits;
+    splits = (groups + per - 1) / per;
+    mvf::Args args{y.hdr, a.hdr, a.words, x.hdr, x.words, m, n,
+                   (uint32_t)(per * mvf::kKC), 0u, yv};
+    args.stage_region = (uint32_t)(warps * mvf::kStages * 32 * mvf::pitch_bytes(bmax_a));
+    const size_t smem = args.stage_region + per * mvf::kKC * sizeof(int);
+    dim3 grid((unsigned)row_blocks, (unsigned)splits);
+    profile_begin(st);
+    if (bmax_a <= 8)
+      mvf::launch_matvec_fast8(args, grid, warps * 32, smem, st);
+    else if (bmax_a <= 16)
+      mvf::launch_matvec_fast16(args, grid, warps * 32, smem, st);
+    else
+      mvf::launch_matvec_fast32(args, grid, warps * 32, smem, st);
+    profile_end(st);
+    note_launch();
+    run_pack_scratch(yv, y, st);
+    return;
+  }
   if (n) {
     int g = (int)umin((n + 255) / 256, (uint64_t)num_sms() * 4);
     k_decode_vec<<<g, 256, 0, st>>>(y.hdr, x.hdr, x.words, n, xs);

@@ -2,10 +2,45 @@
 // width selection + pack of dense int32/int64 matrices, unpack, element
 // access, and the elementwise operations whose results are re-packed by the
 // same engine (add, scale).
-#include "pack_engine.cuh"
+#include "ew_kernels.cuh"
 #include "kernels.h"
+#include "pack_engine.cuh"
 
 namespace ccm {
+
+namespace ge {
+extern template void launch_ew_class<8>(const EwCall& c, cudaStream_t st);
+extern template void launch_ew_class<16>(const EwCall& c, cudaStream_t st);
+extern template void launch_ew_class<32>(const EwCall& c, cudaStream_t st);
+}  // namespace ge
+
+int width_bound(uint64_t capacity, uint64_t n) {
+  if (n == 0) return 64;
+  return (int)umin(capacity * 32 / n, 64);
+}
+
+int bitlen_host(uint64_t v) {
+  int l = 0;
+  for (; v; v >>= 1) ++l;
+  return l;
+}
+
+namespace {
+
+// Width class of the group-engine kernels for a width bound (0: none, use
+// the run-time-width kernels).
+int ew_class(int bmax) { return bmax <= 8 ? 8 : bmax <= 16 ? 16 : bmax <= 32 ? 32 : 0; }
+
+void launch_ew(int cls, const ge::EwCall& c, cudaStream_t st) {
+  switch (cls) {
+    case 8: ge::launch_ew_class<8>(c, st); break;
+    case 16: ge::launch_ew_class<16>(c, st); break;
+    default: ge::launch_ew_class<32>(c, st); break;
+  }
+  note_launch();
+}
+
+}  // namespace
 
 int num_sms() {
   int dev = 0, sms = 0;
@@ -92,7 +127,24 @@ void run_pack(const void* dense, int dtype, uint64_t rows, uint64_t cols, const 
   ia.out_cols = cols;
   launch_init(ia, st);
   uint64_t n = rows * cols;
-  if (dtype == CCM_I64) {
+  const int cls = ew_class(width_bound(out.capacity, n));
+  if (cls && n) {
+    if (dtype == CCM_I64)
+      launch_stats(ProdDenseI64{(const int64_t*)dense}, out.hdr, n, st);
+    else
+      launch_stats(ProdDenseI32{(const int32_t*)dense}, out.hdr, n, st);
+    ge::EwCall c{};
+    c.kind = dtype == CCM_I64 ? ge::EwKind::PackI64 : ge::EwKind::PackI32;
+    c.dense = dense;
+    c.out = out.hdr;
+    c.words = out.words;
+    c.capacity = out.capacity;
+    c.rows = rows;
+    c.cols = cols;
+    profile_begin(st);
+    launch_ew(cls, c, st);
+    profile_end(st);
+  } else if (dtype == CCM_I64) {
     ProdDenseI64 p{(const int64_t*)dense};
     if (n) launch_stats(p, out.hdr, n, st);
     profile_begin(st);
@@ -130,6 +182,22 @@ __global__ void __launch_bounds__(256) k_unpack(const ccm_header* h, const uint3
 
 void run_unpack(const ccm_matrix& a, void* dense, int dtype, int32_t* err, cudaStream_t st) {
   uint64_t n = a.rows * a.cols;
+  const int cls = ew_class(width_bound(a.capacity, n));
+  if (cls && n) {
+    ge::EwCall c{};
+    c.kind = dtype == CCM_I64 ? ge::EwKind::UnpackI64 : ge::EwKind::UnpackI32;
+    c.dense = dense;
+    c.out = a.hdr;
+    c.words = a.words;
+    c.capacity = a.capacity;
+    c.rows = a.rows;
+    c.cols = a.cols;
+    c.err = err;
+    profile_begin(st);
+    launch_ew(cls, c, st);
+    profile_end(st);
+    return;
+  }
   int grid = (int)umin(umax((n + 255) / 256, 1), (uint64_t)num_sms() * 16);
   profile_begin(st);
   if (dtype == CCM_I64)
@@ -202,8 +270,29 @@ void run_add(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, cuda
   ia.out_rows = c.rows;
   ia.out_cols = c.cols;
   launch_init(ia, st);
-  ProdAdd p{{a.hdr, a.words, 0, 0}, {b.hdr, b.words, 0, 0}};
   uint64_t n = c.rows * c.cols;
+  const int cls = ew_class(max(max(width_bound(a.capacity, n), width_bound(b.capacity, n)),
+                               width_bound(c.capacity, n)));
+  if (cls && n) {
+    ge::EwCall e{};
+    e.ha = a.hdr;
+    e.wa = a.words;
+    e.hb = b.hdr;
+    e.wb = b.words;
+    e.out = c.hdr;
+    e.words = c.words;
+    e.capacity = c.capacity;
+    e.rows = c.rows;
+    e.cols = c.cols;
+    e.kind = ge::EwKind::AddStats;
+    launch_ew(cls, e, st);
+    e.kind = ge::EwKind::AddPack;
+    profile_begin(st);
+    launch_ew(cls, e, st);
+    profile_end(st);
+    return;
+  }
+  ProdAdd p{{a.hdr, a.words, 0, 0}, {b.hdr, b.words, 0, 0}};
   if (n) launch_stats(p, c.hdr, n, st);
   profile_begin(st);
   launch_pack(p, c.hdr, c.words, c.capacity, n, st);
@@ -220,8 +309,27 @@ void run_scale(const ccm_matrix& a, int64_t s, const ccm_matrix& c, cudaStream_t
   ia.out_rows = c.rows;
   ia.out_cols = c.cols;
   launch_init(ia, st);
-  ProdScale p{{a.hdr, a.words, 0, 0}, s};
   uint64_t n = c.rows * c.cols;
+  const int cls = ew_class(max(width_bound(a.capacity, n), width_bound(c.capacity, n)));
+  if (cls && n) {
+    ge::EwCall e{};
+    e.ha = a.hdr;
+    e.wa = a.words;
+    e.s = s;
+    e.out = c.hdr;
+    e.words = c.words;
+    e.capacity = c.capacity;
+    e.rows = c.rows;
+    e.cols = c.cols;
+    e.kind = ge::EwKind::ScaleStats;
+    launch_ew(cls, e, st);
+    e.kind = ge::EwKind::ScalePack;
+    profile_begin(st);
+    launch_ew(cls, e, st);
+    profile_end(st);
+    return;
+  }
+  ProdScale p{{a.hdr, a.words, 0, 0}, s};
   if (n) launch_stats(p, c.hdr, n, st);
   profile_begin(st);
   launch_pack(p, c.hdr, c.words, c.capacity, n, st);
@@ -232,6 +340,20 @@ void run_scale(const ccm_matrix& a, int64_t s, const ccm_matrix& c, cudaStream_t
 void run_pack_scratch(const int64_t* vals, const ccm_matrix& out, cudaStream_t st) {
   ProdDenseI64 p{vals};
   uint64_t n = out.rows * out.cols;
+  const int cls = ew_class(width_bound(out.capacity, n));
+  if (cls && n) {
+    launch_stats(p, out.hdr, n, st);
+    ge::EwCall c{};
+    c.kind = ge::EwKind::PackI64;
+    c.dense = vals;
+    c.out = out.hdr;
+    c.words = out.words;
+    c.capacity = out.capacity;
+    c.rows = out.rows;
+    c.cols = out.cols;
+    launch_ew(cls, c, st);
+    return;
+  }
   if (n) launch_stats(p, out.hdr, n, st);
   launch_pack(p, out.hdr, out.words, out.capacity, n, st);
 }

@@ -25,10 +25,12 @@ def _rand(seed, shape, b, signed=True):
     else:
         v = synth.uniform_int(seed, 0, n, 0, (1 << b) - 1 if b < 63 else (1 << 63) - 1)
     v = v.reshape(shape)
-    if n:
-        lo, hi = synth.signed_range(b) if signed else (0, (1 << min(b, 63)) - 1)
+    lo, hi = synth.signed_range(b) if signed else (0, (1 << min(b, 63)) - 1)
+    if n >= 2:
         v.flat[0] = lo
         v.flat[-1] = hi
+    elif n == 1:
+        v.flat[0] = lo if signed else hi  # the one entry alone fixes the width at b
     return v
 
 
@@ -189,10 +191,17 @@ def test_matvec_pr1(ccm):
 @pytest.mark.parametrize("b", [1, 4, 8, 12, 16, 31])
 def test_matmul(ccm, path, m, k, n, b):
     a, bm = _rand(m + k + b, (m, k), b), _rand(n + b, (k, n), b)
-    o = oracle.matmul(oracle.pack(a), oracle.pack(bm))
+    try:
+        o = oracle.matmul(oracle.pack(a), oracle.pack(bm))
+    except OverflowError:
+        o = None
     p = ccm.MATMUL_CUDACORE if path == "cuda" else ccm.MATMUL_AUTO
-    c = ccm.matmul(ccm.pack(to_dev(a)), ccm.pack(to_dev(bm)), path=p)
-    assert_same_packed(c, o, f"matmul {path} {m}x{k}x{n} b={b}")
+    c = ccm.matmul(ccm.pack(to_dev(a)), ccm.pack(to_dev(bm)), path=p,
+                   capacity=ccm.words_for(m, n, 64))
+    if o is None:
+        assert c.status == ccm.E_OVERFLOW
+    else:
+        assert_same_packed(c, o, f"matmul {path} {m}x{k}x{n} b={b}")
 
 
 def test_matmul_identity_and_overflow(ccm):
@@ -229,3 +238,50 @@ def test_device_generator_matches_synth(ccm):
     table = torch.from_numpy(synth.poisson_cdf_table(5.0))
     g = ccm.gen_poisson(200000, 1303, 0, table).cpu().numpy()
     assert np.array_equal(g, synth.poisson(1303, 0, 200000, 5.0))
+
+
+# ---------------------------------------------------------------------------
+# Both kernel families agree: the width-class kernels (chosen when the buffer
+# capacities bound the widths) and the run-time-width kernels (chosen when a
+# capacity allows any width up to 64).
+# ---------------------------------------------------------------------------
+def _pack_cap(ccm, a, cap_width):
+    rows, cols = a.shape
+    cap = ccm.words_for(rows, cols, cap_width)
+    return ccm.pack_into(to_dev(a), ccm.PackedMatrix(rows, cols, cap, device()))
+
+
+@pytest.mark.parametrize("b", [1, 2, 3, 5, 7, 8, 9, 12, 16, 17, 24, 31, 32])
+def test_width_class_and_runtime_kernels_agree(ccm, b):
+    shape = (13, 1111)  # 14443 fields: 15 tiles, a ragged last tile
+    a = _rand(b + 1000, shape, b)
+    c = _rand(b + 2000, shape, max(1, b - 1))
+    oa, oc = oracle.pack(a), oracle.pack(c)
+    pa_fast, pa_rt = _pack_cap(ccm, a, b), _pack_cap(ccm, a, 64)
+    pc_fast = _pack_cap(ccm, c, max(1, b - 1))
+    assert_same_packed(pa_fast, oa, f"class pack b={b}")
+    assert_same_packed(pa_rt, oa, f"runtime pack b={b}")
+    assert np.array_equal(ccm.unpack(pa_fast).cpu().numpy(), a)
+    assert np.array_equal(ccm.unpack(pa_fast, dtype=torch.int32).cpu().numpy(), a)
+    s_exp = oracle.add(oa, oc)
+    for cap in (s_exp.width, 64):
+        out = ccm.PackedMatrix(*shape, ccm.words_for(*shape, cap), device())
+        assert_same_packed(ccm.add_into(pa_fast, pc_fast, out), s_exp, f"add b={b} cap={cap}")
+    d_exp = oracle.scale(oa, -3)
+    for cap in (d_exp.width, 64):
+        out = ccm.PackedMatrix(*shape, ccm.words_for(*shape, cap), device())
+        assert_same_packed(ccm.scale_into(pa_fast, -3, out), d_exp, f"scale b={b} cap={cap}")
+
+
+@pytest.mark.parametrize("m,n", [(1, 128), (31, 256), (300, 384), (257, 1280), (1000, 128)])
+@pytest.mark.parametrize("ba,bx,sa", [(1, 1, 0), (3, 8, 1), (5, 8, 0), (8, 8, 1), (12, 7, 1),
+                                      (16, 8, 0), (17, 8, 1), (24, 16, 1), (31, 8, 0), (32, 8, 1),
+                                      (32, 8, 0)])
+def test_matvec_row_aligned(ccm, m, n, ba, bx, sa):
+    """Row-aligned A (cols % 128 == 0): the streaming kernel vs the oracle."""
+    a = _rand(m + n + ba, (m, n), ba, bool(sa))
+    x = _rand(bx + n, (n, 1), bx)
+    o = oracle.matvec(oracle.pack(a), oracle.pack(x))
+    pa, px = _pack_cap(ccm, a, ba), _pack_cap(ccm, x, bx)
+    y = ccm.matvec(pa, px, capacity=ccm.words_for(m, 1, 64))
+    assert_same_packed(y, o, f"matvec aligned {m}x{n} b={ba}/{bx}")
