@@ -94,8 +94,8 @@ typedef struct ccm_header {
 } ccm_header;
 
 /* Host-side handle of one packed matrix: where it lives and its shape.
- * `hdr` and `words` are device pointers; `capacity` counts the uint32 words
- * available at `words`.  `rows`/`cols` are the shape the caller expects; the
+ * `hdr` and `words` are device pointers, both 16-byte aligned; `capacity`
+ * counts the uint32 words available at `words`.  `rows`/`cols` are the shape the caller expects; the
  * library checks them against each other on the host and against the header
  * on the GPU. */
 typedef struct ccm_matrix {

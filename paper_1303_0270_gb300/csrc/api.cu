@@ -25,7 +25,8 @@ bool valid_out(const ccm_matrix* m) {
 bool valid_in(const ccm_matrix* m) {
   if (!m || !m->hdr) return false;
   if (m->rows * m->cols && !m->words) return false;
-  return reinterpret_cast<uintptr_t>(m->hdr) % 16 == 0;
+  return reinterpret_cast<uintptr_t>(m->hdr) % 16 == 0 &&
+         reinterpret_cast<uintptr_t>(m->words) % 16 == 0;
 }
 
 ccm_status launched() {

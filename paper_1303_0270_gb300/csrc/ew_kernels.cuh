@@ -10,13 +10,27 @@
 // the width back from the header and writes the fields.  Operations on
 // packed inputs recompute their values in the pack pass instead of keeping
 // them: re-reading b-bit inputs costs less than writing and reading int64.
+//
+// Memory-level parallelism: a warp loads the words of its next tile into
+// registers (16-byte loads) while it decodes the current one, so every warp
+// keeps one tile of every input in flight.
 #pragma once
+
+#include <type_traits>
 
 #include "group_engine.cuh"
 #include "pack_engine.cuh"
 
 namespace ccm {
 namespace ge {
+
+// Words of one packed input tile held in registers: Q 16-byte vectors per
+// lane cover the 32*b <= 8*BMAX... words of a tile for b <= BMAX.
+template <int BMAX>
+struct TileRegs {
+  static constexpr int Q = (BMAX + 3) / 4;  // uint4 per lane: 32*BMAX words / 4 / 32
+  uint4 r[Q];
+};
 
 struct PackedIn {
   const ccm_header* h;
@@ -28,41 +42,86 @@ struct PackedIn {
     sgn = h->is_signed;
     dw = data_words(n, b);
   }
-};
-
-template <typename T>
-struct OpDense {
-  const T* __restrict__ p;
-  __device__ __forceinline__ void init(uint64_t) {}
+  // Global -> registers: uint4 index lane + 32 j of the tile (zero past the end).
   template <int BMAX>
-  __device__ __forceinline__ void produce(uint32_t* buf, uint64_t tile, uint32_t nt, int lane,
-                                          int64_t (&v)[32], int&) const {
-    T* tb = reinterpret_cast<T*>(buf);
-    stage_dense<T>(tb, p, tile * kTile, nt, lane);
-    __syncwarp();
+  __device__ __forceinline__ void load(TileRegs<BMAX>& t, uint64_t tile, int lane) const {
+    const uint64_t w0 = tile * (uint64_t)(32 * b);
+    const int nq = 8 * b;  // uint4 per tile
+    const bool whole = w0 + 32 * (uint64_t)b <= dw;
 #pragma unroll
-    for (int k = 0; k < 32; ++k) v[k] = (int64_t)tb[33 * lane + k];
-    __syncwarp();
+    for (int j = 0; j < TileRegs<BMAX>::Q; ++j) {
+      const int q = lane + 32 * j;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (q < nq) {
+        if (whole) {
+          v = __ldg(reinterpret_cast<const uint4*>(w + w0) + q);
+        } else {
+          const uint64_t g = w0 + 4 * (uint64_t)q;
+          if (g < dw) v.x = __ldg(w + g);
+          if (g + 1 < dw) v.y = __ldg(w + g + 1);
+          if (g + 2 < dw) v.z = __ldg(w + g + 2);
+          if (g + 3 < dw) v.w = __ldg(w + g + 3);
+        }
+      }
+      t.r[j] = v;
+    }
+  }
+  // Registers -> shared staging layout.
+  template <int BMAX>
+  __device__ __forceinline__ void stage(const TileRegs<BMAX>& t, uint32_t* buf, int lane) const {
+    const int nq = 8 * b;
+#pragma unroll
+    for (int j = 0; j < TileRegs<BMAX>::Q; ++j) {
+      const int q = lane + 32 * j;
+      if (q < nq) {
+        const int w = 4 * q;
+        buf[stage_pos(w, b)] = t.r[j].x;
+        buf[stage_pos(w + 1, b)] = t.r[j].y;
+        buf[stage_pos(w + 2, b)] = t.r[j].z;
+        buf[stage_pos(w + 3, b)] = t.r[j].w;
+      }
+    }
   }
 };
 
+constexpr int kRegion = kBufWords / 2;  // 1056 words: one packed tile of width <= 32
+
+// ---------------------------------------------------------------------------
+// Operations.  produce() hands every field value of the lane's group to
+// sink(k, value); loads for the next tile are issued by prefetch().
+// ---------------------------------------------------------------------------
 struct OpAdd {
   PackedIn a, b;
+  template <int BMAX>
+  struct Regs {
+    TileRegs<BMAX> ra, rb;
+  };
   __device__ __forceinline__ void init(uint64_t n) {
     a.init(n);
     b.init(n);
   }
   template <int BMAX>
-  __device__ __forceinline__ void produce(uint32_t* buf, uint64_t tile, uint32_t, int lane,
-                                          int64_t (&v)[32], int& ovf) const {
-    stage_packed(buf, a.w, tile, a.b, a.dw, lane);
+  __device__ __forceinline__ void prefetch(Regs<BMAX>& r, uint64_t tile, int lane) const {
+    a.load(r.ra, tile, lane);
+    b.load(r.rb, tile, lane);
+  }
+  template <int BMAX, class Sink>
+  __device__ __forceinline__ void produce(const Regs<BMAX>& r, uint32_t* buf, int lane,
+                                          int& ovf, Sink&& sink) const {
+    uint32_t* ba = buf;
+    uint32_t* bb = buf + kRegion;
+    a.stage(r.ra, ba, lane);
+    b.stage(r.rb, bb, lane);
     __syncwarp();
-    decode_dispatch<BMAX>(a.b, a.sgn, buf, lane, [&](int k, int64_t x) { v[k] = x; });
-    __syncwarp();
-    stage_packed(buf, b.w, tile, b.b, b.dw, lane);
-    __syncwarp();
-    decode_dispatch<BMAX>(b.b, b.sgn, buf, lane,
-                          [&](int k, int64_t x) { v[k] = add_checked(v[k], x, ovf); });
+    using V = typename std::conditional<(BMAX <= 16), int32_t, int64_t>::type;
+    V va[32];
+    decode_dispatch<BMAX>(a.b, a.sgn, ba, lane, [&](int k, int64_t x) { va[k] = (V)x; });
+    decode_dispatch<BMAX>(b.b, b.sgn, bb, lane, [&](int k, int64_t x) {
+      if constexpr (BMAX <= 16)
+        sink(k, (int64_t)va[k] + x);  // |sum| < 2^17: no overflow
+      else
+        sink(k, add_checked((int64_t)va[k], x, ovf));
+    });
     __syncwarp();
   }
 };
@@ -70,20 +129,28 @@ struct OpAdd {
 struct OpScale {
   PackedIn a;
   int64_t s;
+  template <int BMAX>
+  struct Regs {
+    TileRegs<BMAX> ra;
+  };
   __device__ __forceinline__ void init(uint64_t n) { a.init(n); }
   template <int BMAX>
-  __device__ __forceinline__ void produce(uint32_t* buf, uint64_t tile, uint32_t, int lane,
-                                          int64_t (&v)[32], int& ovf) const {
-    stage_packed(buf, a.w, tile, a.b, a.dw, lane);
+  __device__ __forceinline__ void prefetch(Regs<BMAX>& r, uint64_t tile, int lane) const {
+    a.load(r.ra, tile, lane);
+  }
+  template <int BMAX, class Sink>
+  __device__ __forceinline__ void produce(const Regs<BMAX>& r, uint32_t* buf, int lane,
+                                          int& ovf, Sink&& sink) const {
+    a.stage(r.ra, buf, lane);
     __syncwarp();
     const int64_t sc = s;
     decode_dispatch<BMAX>(a.b, a.sgn, buf, lane,
-                          [&](int k, int64_t x) { v[k] = mul_checked(x, sc, ovf); });
+                          [&](int k, int64_t x) { sink(k, mul_checked(x, sc, ovf)); });
     __syncwarp();
   }
 };
 
-// Statistics (PACK = false) or pack (PACK = true) pass of an operation.
+// Statistics (PACK = false) or pack (PACK = true) pass of add / scale.
 template <class Op, int BMAX, bool PACK>
 __global__ void __launch_bounds__(kThreads) k_ew(Op op, ccm_header* out, uint32_t* words,
                                                  uint64_t capacity, uint64_t n) {
@@ -104,30 +171,31 @@ __global__ void __launch_bounds__(kThreads) k_ew(Op op, ccm_header* out, uint32_
   uint64_t orv = 0;
   uint32_t neg = 0;
   int ovf = 0;
-  for (uint64_t tile = (uint64_t)blockIdx.x * kWarps + warp; tile < ntiles; tile += gwarps) {
+  uint64_t tile = (uint64_t)blockIdx.x * kWarps + warp;
+  typename Op::template Regs<BMAX> cur, nxt;
+  if (tile < ntiles) op.template prefetch<BMAX>(cur, tile, lane);
+  for (; tile < ntiles; tile += gwarps) {
+    if (tile + gwarps < ntiles) op.template prefetch<BMAX>(nxt, tile + gwarps, lane);
     const uint32_t nt = (uint32_t)umin((uint64_t)kTile, n - tile * kTile);
-    int64_t v[32];
-    op.template produce<BMAX>(buf, tile, nt, lane, v, ovf);
-    if ((uint32_t)(32 * lane + 32) > nt) {
-#pragma unroll
-      for (int k = 0; k < 32; ++k)
-        if ((uint32_t)(32 * lane + k) >= nt) v[k] = 0;
-    }
+    const int first = 32 * lane;  // the lane's first field in the tile
     if constexpr (!PACK) {
-#pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        orv |= fold(v[k]);
-        neg |= (uint32_t)(v[k] < 0);
-      }
+      op.template produce<BMAX>(cur, buf, lane, ovf, [&](int k, int64_t v) {
+        if (first + k < (int)nt) {
+          orv |= fold(v);
+          neg |= (uint32_t)(v < 0);
+        }
+      });
     } else {
       uint32_t u[32];
-#pragma unroll
-      for (int k = 0; k < 32; ++k) u[k] = (uint32_t)v[k] & mask;
+      op.template produce<BMAX>(cur, buf, lane, ovf, [&](int k, int64_t v) {
+        u[k] = first + k < (int)nt ? ((uint32_t)v & mask) : 0u;
+      });
       encode_dispatch<BMAX>(b, u, buf, lane);
       __syncwarp();
       store_packed(buf, words, tile, b, dw, lane);
       __syncwarp();
     }
+    cur = nxt;
   }
   if constexpr (!PACK) {
     orv = warp_or64(orv);
@@ -138,6 +206,36 @@ __global__ void __launch_bounds__(kThreads) k_ew(Op op, ccm_header* out, uint32_
       if (neg) atomicOr(&out->stat_neg, 1u);
       if (ovf) set_status(out, CCM_E_OVERFLOW);
     }
+  }
+}
+
+// Pack pass of a dense int32/int64 matrix (its statistics come from k_stats).
+template <typename T, int BMAX>
+__global__ void __launch_bounds__(kThreads) k_pack_dense(const T* __restrict__ src,
+                                                         ccm_header* out, uint32_t* words,
+                                                         uint64_t capacity, uint64_t n) {
+  __shared__ __align__(16) uint32_t s_buf[kWarps][kBufWords];
+  int b, sgn;
+  if (!resolve_output(out, words, capacity, n, b, sgn)) return;
+  const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+  uint32_t* buf = s_buf[warp];
+  T* tb = reinterpret_cast<T*>(buf);
+  const uint64_t dw = data_words(n, b);
+  const uint32_t mask = b >= 32 ? 0xffffffffu : ((1u << b) - 1u);
+  const uint64_t ntiles = (n + kTile - 1) / kTile;
+  const uint64_t gwarps = (uint64_t)gridDim.x * kWarps;
+  for (uint64_t tile = (uint64_t)blockIdx.x * kWarps + warp; tile < ntiles; tile += gwarps) {
+    const uint32_t nt = (uint32_t)umin((uint64_t)kTile, n - tile * kTile);
+    stage_dense<T>(tb, src, tile * kTile, nt, lane);
+    __syncwarp();
+    uint32_t u[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) u[k] = (uint32_t)tb[33 * lane + k] & mask;
+    __syncwarp();
+    encode_dispatch<BMAX>(b, u, buf, lane);
+    __syncwarp();
+    store_packed(buf, words, tile, b, dw, lane);
+    __syncwarp();
   }
 }
 
@@ -194,25 +292,26 @@ struct EwCall {
   int32_t* err;           // unpack status
 };
 
-inline int ew_grid(uint64_t n) {
+inline int ew_grid(uint64_t n, int per_sm) {
   uint64_t tiles = (n + kTile - 1) / kTile;
   uint64_t want = (tiles + kWarps - 1) / kWarps;
-  return (int)umin(umax(want, 1), (uint64_t)num_sms() * 12);
+  return (int)umin(umax(want, 1), (uint64_t)num_sms() * per_sm);
 }
 
 template <int C>
 void launch_ew_class(const EwCall& c, cudaStream_t st) {
   const uint64_t n = c.rows * c.cols;
-  const int g = ew_grid(n);
   PackedIn a{c.ha, c.wa, 0, 0, 0}, b{c.hb, c.wb, 0, 0, 0};
+  // Persistent-style grids: every warp keeps walking tiles (and prefetching).
+  const int g = ew_grid(n, 8);
   switch (c.kind) {
     case EwKind::PackI64:
-      k_ew<OpDense<int64_t>, C, true><<<g, kThreads, 0, st>>>(
-          OpDense<int64_t>{(const int64_t*)c.dense}, c.out, c.words, c.capacity, n);
+      k_pack_dense<int64_t, C><<<ew_grid(n, 12), kThreads, 0, st>>>(
+          (const int64_t*)c.dense, c.out, c.words, c.capacity, n);
       break;
     case EwKind::PackI32:
-      k_ew<OpDense<int32_t>, C, true><<<g, kThreads, 0, st>>>(
-          OpDense<int32_t>{(const int32_t*)c.dense}, c.out, c.words, c.capacity, n);
+      k_pack_dense<int32_t, C><<<ew_grid(n, 12), kThreads, 0, st>>>(
+          (const int32_t*)c.dense, c.out, c.words, c.capacity, n);
       break;
     case EwKind::AddStats:
       k_ew<OpAdd, C, false><<<g, kThreads, 0, st>>>(OpAdd{a, b}, c.out, nullptr, 0, n);
@@ -227,12 +326,12 @@ void launch_ew_class(const EwCall& c, cudaStream_t st) {
       k_ew<OpScale, C, true><<<g, kThreads, 0, st>>>(OpScale{a, c.s}, c.out, c.words, c.capacity, n);
       break;
     case EwKind::UnpackI64:
-      k_unpack_ge<int64_t, C><<<g, kThreads, 0, st>>>(c.out, c.words, c.rows, c.cols, c.capacity,
-                                                      (int64_t*)c.dense, c.err);
+      k_unpack_ge<int64_t, C><<<ew_grid(n, 12), kThreads, 0, st>>>(
+          c.out, c.words, c.rows, c.cols, c.capacity, (int64_t*)c.dense, c.err);
       break;
     case EwKind::UnpackI32:
-      k_unpack_ge<int32_t, C><<<g, kThreads, 0, st>>>(c.out, c.words, c.rows, c.cols, c.capacity,
-                                                      (int32_t*)c.dense, c.err);
+      k_unpack_ge<int32_t, C><<<ew_grid(n, 12), kThreads, 0, st>>>(
+          c.out, c.words, c.rows, c.cols, c.capacity, (int32_t*)c.dense, c.err);
       break;
   }
 }
