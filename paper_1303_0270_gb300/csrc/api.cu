@@ -118,7 +118,13 @@ ccm_status ccm_scale(const ccm_matrix* a, int64_t s, const ccm_matrix* c, ccm_st
 size_t ccm_workspace_bytes(int op, uint64_t m, uint64_t k, uint64_t n) {
   switch (op) {
     case CCM_OP_MATVEC: return ccm::matvec_workspace(m, k);
-    case CCM_OP_MATMUL: return ccm::matmul_workspace(m, k, n);
+    case CCM_OP_MATMUL: {
+      // the tensor path's digit planes depend on the operand widths, which a
+      // shape-only query cannot see: size for the widest it accepts (16 bits)
+      ccm_matrix a{nullptr, nullptr, ccm::words_for(m * k, 16), m, k};
+      ccm_matrix b{nullptr, nullptr, ccm::words_for(k * n, 16), k, n};
+      return ccm::matmul_workspace(a, b);
+    }
     default: return 0;
   }
 }
@@ -143,7 +149,7 @@ ccm_status ccm_matmul(const ccm_matrix* a, const ccm_matrix* b, const ccm_matrix
   if (reinterpret_cast<uintptr_t>(ws) % 256) return CCM_E_INVAL;
   if (b->rows != a->cols || c->rows != a->rows || c->cols != b->cols) return CCM_E_SHAPE;
   if (!capacity_ok(c)) return CCM_E_CAPACITY;
-  if (ws_bytes < ccm::matmul_workspace(a->rows, a->cols, b->cols)) return CCM_E_CAPACITY;
+  if (ws_bytes < ccm::matmul_workspace(*a, *b)) return CCM_E_CAPACITY;
   int st = ccm::run_matmul(*a, *b, *c, path, ws, to_cuda(stream));
   if (st != CCM_OK) return (ccm_status)st;
   return launched();

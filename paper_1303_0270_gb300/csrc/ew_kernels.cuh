@@ -88,10 +88,16 @@ constexpr int kRegion = kBufWords / 2;  // 1056 words: one packed tile of width 
 
 // ---------------------------------------------------------------------------
 // Operations.  produce() hands every field value of the lane's group to
-// sink(k, value); loads for the next tile are issued by prefetch().
+// sink(k, value) as Val<BMAX> (int32 when the class bounds every value below
+// 2^31, int64 otherwise); loads for the next tile are issued by prefetch().
+// Fields past the end of the matrix need no masking: they decode from the
+// zero bits above the last field (a packed matrix is canonical) or from the
+// zero fill of words past the end, and give 0 in every operation.
 // ---------------------------------------------------------------------------
 struct OpAdd {
   PackedIn a, b;
+  template <int BMAX>
+  using Val = typename std::conditional<(BMAX <= 16), int32_t, int64_t>::type;
   template <int BMAX>
   struct Regs {
     TileRegs<BMAX> ra, rb;
@@ -108,27 +114,32 @@ struct OpAdd {
   template <int BMAX, class Sink>
   __device__ __forceinline__ void produce(const Regs<BMAX>& r, uint32_t* buf, int lane,
                                           int& ovf, Sink&& sink) const {
+    using V = Val<BMAX>;
     uint32_t* ba = buf;
     uint32_t* bb = buf + kRegion;
     a.stage(r.ra, ba, lane);
     b.stage(r.rb, bb, lane);
     __syncwarp();
-    using V = typename std::conditional<(BMAX <= 16), int32_t, int64_t>::type;
     V va[32];
     decode_dispatch<BMAX>(a.b, a.sgn, ba, lane, [&](int k, int64_t x) { va[k] = (V)x; });
     decode_dispatch<BMAX>(b.b, b.sgn, bb, lane, [&](int k, int64_t x) {
       if constexpr (BMAX <= 16)
-        sink(k, (int64_t)va[k] + x);  // |sum| < 2^17: no overflow
+        sink(k, (V)(va[k] + (V)x));  // |sum| < 2^17
       else
-        sink(k, add_checked((int64_t)va[k], x, ovf));
+        sink(k, (V)add_checked((int64_t)va[k], x, ovf));
     });
     __syncwarp();
   }
 };
 
+// SMALL: the host checked |s| < 2^15, so in the classes up to 16 bits every
+// product stays below 2^31 and is computed in 32 bits.
+template <bool SMALL>
 struct OpScale {
   PackedIn a;
   int64_t s;
+  template <int BMAX>
+  using Val = typename std::conditional<(SMALL && BMAX <= 16), int32_t, int64_t>::type;
   template <int BMAX>
   struct Regs {
     TileRegs<BMAX> ra;
@@ -141,11 +152,16 @@ struct OpScale {
   template <int BMAX, class Sink>
   __device__ __forceinline__ void produce(const Regs<BMAX>& r, uint32_t* buf, int lane,
                                           int& ovf, Sink&& sink) const {
+    using V = Val<BMAX>;
     a.stage(r.ra, buf, lane);
     __syncwarp();
     const int64_t sc = s;
-    decode_dispatch<BMAX>(a.b, a.sgn, buf, lane,
-                          [&](int k, int64_t x) { sink(k, mul_checked(x, sc, ovf)); });
+    decode_dispatch<BMAX>(a.b, a.sgn, buf, lane, [&](int k, int64_t x) {
+      if constexpr (sizeof(V) == 4)
+        sink(k, (V)((int32_t)x * (int32_t)sc));
+      else
+        sink(k, mul_checked(x, sc, ovf));
+    });
     __syncwarp();
   }
 };
@@ -154,6 +170,9 @@ struct OpScale {
 template <class Op, int BMAX, bool PACK>
 __global__ void __launch_bounds__(kThreads) k_ew(Op op, ccm_header* out, uint32_t* words,
                                                  uint64_t capacity, uint64_t n) {
+  using V = typename Op::template Val<BMAX>;
+  using U = typename std::make_unsigned<V>::type;
+  constexpr int kSignShift = 8 * sizeof(V) - 1;
   __shared__ __align__(16) uint32_t s_buf[kWarps][kBufWords];
   int b = 0, sgn = 0;
   if constexpr (PACK) {
@@ -168,28 +187,22 @@ __global__ void __launch_bounds__(kThreads) k_ew(Op op, ccm_header* out, uint32_
   const uint32_t mask = b >= 32 ? 0xffffffffu : ((1u << b) - 1u);
   const uint64_t ntiles = (n + kTile - 1) / kTile;
   const uint64_t gwarps = (uint64_t)gridDim.x * kWarps;
-  uint64_t orv = 0;
-  uint32_t neg = 0;
+  U orv = 0;  // OR of (v >= 0 ? v : ~v)
+  V negv = 0;  // OR of the values: negative iff some value is
   int ovf = 0;
   uint64_t tile = (uint64_t)blockIdx.x * kWarps + warp;
   typename Op::template Regs<BMAX> cur, nxt;
   if (tile < ntiles) op.template prefetch<BMAX>(cur, tile, lane);
   for (; tile < ntiles; tile += gwarps) {
     if (tile + gwarps < ntiles) op.template prefetch<BMAX>(nxt, tile + gwarps, lane);
-    const uint32_t nt = (uint32_t)umin((uint64_t)kTile, n - tile * kTile);
-    const int first = 32 * lane;  // the lane's first field in the tile
     if constexpr (!PACK) {
-      op.template produce<BMAX>(cur, buf, lane, ovf, [&](int k, int64_t v) {
-        if (first + k < (int)nt) {
-          orv |= fold(v);
-          neg |= (uint32_t)(v < 0);
-        }
+      op.template produce<BMAX>(cur, buf, lane, ovf, [&](int, V v) {
+        orv |= (U)(v ^ (v >> kSignShift));
+        negv |= v;
       });
     } else {
       uint32_t u[32];
-      op.template produce<BMAX>(cur, buf, lane, ovf, [&](int k, int64_t v) {
-        u[k] = first + k < (int)nt ? ((uint32_t)v & mask) : 0u;
-      });
+      op.template produce<BMAX>(cur, buf, lane, ovf, [&](int k, V v) { u[k] = (uint32_t)v & mask; });
       encode_dispatch<BMAX>(b, u, buf, lane);
       __syncwarp();
       store_packed(buf, words, tile, b, dw, lane);
@@ -198,11 +211,11 @@ __global__ void __launch_bounds__(kThreads) k_ew(Op op, ccm_header* out, uint32_
     cur = nxt;
   }
   if constexpr (!PACK) {
-    orv = warp_or64(orv);
-    neg = __reduce_or_sync(0xffffffffu, neg);
+    uint64_t o = warp_or64((uint64_t)orv);
+    uint32_t neg = __reduce_or_sync(0xffffffffu, (uint32_t)(negv < 0));
     ovf = (int)__reduce_or_sync(0xffffffffu, (uint32_t)ovf);
     if (lane == 0) {
-      if (orv) atomicOr(reinterpret_cast<unsigned long long*>(&out->stat_or), (unsigned long long)orv);
+      if (o) atomicOr(reinterpret_cast<unsigned long long*>(&out->stat_or), (unsigned long long)o);
       if (neg) atomicOr(&out->stat_neg, 1u);
       if (ovf) set_status(out, CCM_E_OVERFLOW);
     }
@@ -320,10 +333,20 @@ void launch_ew_class(const EwCall& c, cudaStream_t st) {
       k_ew<OpAdd, C, true><<<g, kThreads, 0, st>>>(OpAdd{a, b}, c.out, c.words, c.capacity, n);
       break;
     case EwKind::ScaleStats:
-      k_ew<OpScale, C, false><<<g, kThreads, 0, st>>>(OpScale{a, c.s}, c.out, nullptr, 0, n);
+      if (c.s > -32768 && c.s < 32768)
+        k_ew<OpScale<true>, C, false><<<g, kThreads, 0, st>>>(OpScale<true>{a, c.s}, c.out,
+                                                               nullptr, 0, n);
+      else
+        k_ew<OpScale<false>, C, false><<<g, kThreads, 0, st>>>(OpScale<false>{a, c.s}, c.out,
+                                                                nullptr, 0, n);
       break;
     case EwKind::ScalePack:
-      k_ew<OpScale, C, true><<<g, kThreads, 0, st>>>(OpScale{a, c.s}, c.out, c.words, c.capacity, n);
+      if (c.s > -32768 && c.s < 32768)
+        k_ew<OpScale<true>, C, true><<<g, kThreads, 0, st>>>(OpScale<true>{a, c.s}, c.out,
+                                                              c.words, c.capacity, n);
+      else
+        k_ew<OpScale<false>, C, true><<<g, kThreads, 0, st>>>(OpScale<false>{a, c.s}, c.out,
+                                                               c.words, c.capacity, n);
       break;
     case EwKind::UnpackI64:
       k_unpack_ge<int64_t, C><<<ew_grid(n, 12), kThreads, 0, st>>>(

@@ -132,32 +132,43 @@ __device__ __forceinline__ void encode_group(const uint32_t (&u)[32], uint32_t* 
   for (int j = 0; j < B; ++j) buf[stage_pos(lane * B + j, B)] = w[j];
 }
 
-// Run-time dispatch over the instances up to BMAX.
-template <int BMAX, int B = 1, class F>
+// Run-time dispatch over the instances up to BMAX: one switch (a jump table)
+// on 2*b + sign.
+#define CCM_GE_CASES_8(M) M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8)
+#define CCM_GE_CASES_16(M) CCM_GE_CASES_8(M) M(9) M(10) M(11) M(12) M(13) M(14) M(15) M(16)
+#define CCM_GE_CASES_32(M)                                                                     \
+  CCM_GE_CASES_16(M) M(17) M(18) M(19) M(20) M(21) M(22) M(23) M(24) M(25) M(26) M(27) M(28) \
+  M(29) M(30) M(31) M(32)
+
+template <int BMAX, class F>
 __device__ __forceinline__ void decode_dispatch(int b, int sgn, const uint32_t* buf, int lane,
                                                 F&& fn) {
-  if constexpr (B <= BMAX) {
-    if (b == B) {
-      if (sgn)
-        decode_group<B, true>(buf, lane, fn);
-      else
-        decode_group<B, false>(buf, lane, fn);
-      return;
-    }
-    decode_dispatch<BMAX, B + 1>(b, sgn, buf, lane, fn);
+#define CCM_GE_DEC(B)                                            \
+  case 2 * B:                                                    \
+    if constexpr (B <= BMAX) decode_group<B, false>(buf, lane, fn); \
+    break;                                                       \
+  case 2 * B + 1:                                                \
+    if constexpr (B <= BMAX) decode_group<B, true>(buf, lane, fn);  \
+    break;
+  switch (2 * b + sgn) {
+    CCM_GE_CASES_32(CCM_GE_DEC)
+    default: break;
   }
+#undef CCM_GE_DEC
 }
 
-template <int BMAX, int B = 1>
+template <int BMAX>
 __device__ __forceinline__ void encode_dispatch(int b, const uint32_t (&u)[32], uint32_t* buf,
                                                 int lane) {
-  if constexpr (B <= BMAX) {
-    if (b == B) {
-      encode_group<B>(u, buf, lane);
-      return;
-    }
-    encode_dispatch<BMAX, B + 1>(b, u, buf, lane);
+#define CCM_GE_ENC(B)                                     \
+  case B:                                                 \
+    if constexpr (B <= BMAX) encode_group<B>(u, buf, lane); \
+    break;
+  switch (b) {
+    CCM_GE_CASES_32(CCM_GE_ENC)
+    default: break;
   }
+#undef CCM_GE_ENC
 }
 
 }  // namespace ge

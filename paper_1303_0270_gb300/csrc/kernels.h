@@ -28,13 +28,16 @@ void run_get(const ccm_matrix& a, const uint64_t* idx, uint64_t count, int64_t* 
              cudaStream_t st);
 void run_add(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, cudaStream_t st);
 void run_scale(const ccm_matrix& a, int64_t s, const ccm_matrix& c, cudaStream_t st);
-void run_pack_scratch(const int64_t* vals, const ccm_matrix& out, cudaStream_t st);
+// Packs an int64 result held in scratch; `stats_done` when the producing
+// kernel has already merged the width statistics into out's header.
+void run_pack_scratch(const int64_t* vals, const ccm_matrix& out, cudaStream_t st,
+                      bool stats_done = false);
 
 size_t matvec_workspace(uint64_t m, uint64_t n);
 void run_matvec(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& y, void* ws,
                 cudaStream_t st);
 
-size_t matmul_workspace(uint64_t m, uint64_t k, uint64_t n);
+size_t matmul_workspace(const ccm_matrix& a, const ccm_matrix& b);
 int run_matmul(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, int path, void* ws,
                cudaStream_t st);
 

@@ -98,16 +98,16 @@ __global__ void __launch_bounds__(kMmThreads) k_matmul_cc(ccm_header* out, const
 
 }  // namespace
 
-size_t matmul_workspace(uint64_t m, uint64_t k, uint64_t n) {
+size_t matmul_workspace(const ccm_matrix& a, const ccm_matrix& b) {
+  const uint64_t m = a.rows, n = b.cols;
   size_t c_bytes = ((m * n * sizeof(int64_t)) + 255) & ~(size_t)255;
-  size_t tc = matmul_tc_workspace(m, k, n);
-  return c_bytes + tc + 256;
+  return c_bytes + matmul_tc_workspace(a, b) + 256;
 }
 
 int run_matmul(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, int path, void* ws,
                cudaStream_t st) {
   const uint64_t m = a.rows, k = a.cols, n = b.cols;
-  const bool tc_ok = matmul_tc_supported(m, k, n);
+  const bool tc_ok = matmul_tc_supported(a, b);
   if (path == CCM_MATMUL_TENSOR && !tc_ok) return CCM_E_SHAPE;
   const bool tc = tc_ok && (path == CCM_MATMUL_TENSOR || path == CCM_MATMUL_AUTO);
   int64_t* cs = (int64_t*)ws;
@@ -131,7 +131,10 @@ int run_matmul(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, in
   if (m && n && k) {
     if (tc) {
       size_t c_bytes = ((m * n * sizeof(int64_t)) + 255) & ~(size_t)255;
-      run_matmul_tc(a, b, c, cs, (char*)ws + c_bytes, st);
+      int rc = run_matmul_tc(a, b, c, cs, (char*)ws + c_bytes, st);
+      if (rc != CCM_OK) return rc;
+      run_pack_scratch(cs, c, st, /*stats_done=*/true);
+      return CCM_OK;
     } else {
       uint64_t tiles = ((m + kBM - 1) / kBM) * ((n + kBN - 1) / kBN);
       int g = (int)umin(tiles, (uint64_t)num_sms() * 4);

@@ -137,12 +137,13 @@ void run_matvec(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& y, v
     const size_t smem = args.stage_region + per * mvf::kKC * sizeof(int);
     dim3 grid((unsigned)row_blocks, (unsigned)splits);
     profile_begin(st);
+    const bool narrow = bmax_a + bmax_x + 7 <= 31;
     if (bmax_a <= 8)
-      mvf::launch_matvec_fast8(args, grid, warps * 32, smem, st);
+      mvf::launch_matvec_fast8(args, narrow, grid, warps * 32, smem, st);
     else if (bmax_a <= 16)
-      mvf::launch_matvec_fast16(args, grid, warps * 32, smem, st);
+      mvf::launch_matvec_fast16(args, narrow, grid, warps * 32, smem, st);
     else
-      mvf::launch_matvec_fast32(args, grid, warps * 32, smem, st);
+      mvf::launch_matvec_fast32(args, narrow, grid, warps * 32, smem, st);
     profile_end(st);
     note_launch();
     run_pack_scratch(yv, y, st);

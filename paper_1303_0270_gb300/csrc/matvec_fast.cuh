@@ -66,9 +66,10 @@ __device__ __forceinline__ void issue_stage(const Args& a, uint8_t* buf, uint64_
 
 // Decode 128 fields of width B from the lane's row chunk and accumulate the
 // products with x (int32, 128 entries, broadcast reads).
-template <int B, bool SGN>
+template <int B, bool SGN, bool NARROW>
 __device__ __forceinline__ void decode_mac(const uint8_t* row, const int* __restrict__ xs,
                                            long long& acc) {
+  int acc32 = 0;  // NARROW: 128 products of |a| < 2^ba, |x| < 2^bx with ba + bx + 7 <= 31
   const uint4* rv = reinterpret_cast<const uint4*>(row);
   uint32_t w[4 * B + 1];
 #pragma unroll
@@ -91,6 +92,18 @@ __device__ __forceinline__ void decode_mac(const uint8_t* row, const int* __rest
       const int bit = f * B, wi = bit >> 5, s = bit & 31;
       if constexpr (!SGN && B == 32) {
         acc += (long long)w[wi] * (long long)xa[q];
+      } else if constexpr (NARROW) {
+        uint32_t t;
+        if (s + B <= 32)
+          t = w[wi] >> s;
+        else
+          t = __funnelshift_r(w[wi], w[wi + 1], s);
+        int v;
+        if constexpr (SGN)
+          v = (int)(t << (32 - B)) >> (32 - B);
+        else
+          v = (int)(t & (0xffffffffu >> (32 - B)));
+        acc32 += v * xa[q];
       } else {
         uint32_t t;
         if (s + B <= 32)
@@ -106,9 +119,10 @@ __device__ __forceinline__ void decode_mac(const uint8_t* row, const int* __rest
       }
     }
   }
+  if constexpr (NARROW) acc += acc32;
 }
 
-template <int B, bool SGN>
+template <int B, bool SGN, bool NARROW>
 __device__ __noinline__ void body(const Args& a, uint8_t* smem, int* xs, uint64_t col0,
                                   uint32_t ncols) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -130,7 +144,8 @@ __device__ __noinline__ void body(const Args& a, uint8_t* smem, int* xs, uint64_
       cp_async_commit();
       cp_async_wait<1>();
       __syncwarp();
-      decode_mac<B, SGN>(wbuf + (s % kStages) * stage_bytes + lane * pitch, xs + s * kKC, acc);
+      decode_mac<B, SGN, NARROW>(wbuf + (s % kStages) * stage_bytes + lane * pitch, xs + s * kKC,
+                                 acc);
       __syncwarp();
     }
     if (row0 + lane < a.m)
@@ -140,18 +155,18 @@ __device__ __noinline__ void body(const Args& a, uint8_t* smem, int* xs, uint64_
 }
 
 // Calls body<b, sign> for the runtime width b, for widths up to BMAX.
-template <int BMAX, int B = 1>
+template <int BMAX, bool NARROW, int B = 1>
 __device__ __forceinline__ void dispatch(const Args& a, int b, int sgn, uint8_t* smem, int* xs,
                                          uint64_t col0, uint32_t ncols) {
   if constexpr (B <= BMAX) {
     if (b == B) {
       if (sgn)
-        body<B, true>(a, smem, xs, col0, ncols);
+        body<B, true, NARROW>(a, smem, xs, col0, ncols);
       else
-        body<B, false>(a, smem, xs, col0, ncols);
+        body<B, false, NARROW>(a, smem, xs, col0, ncols);
       return;
     }
-    dispatch<BMAX, B + 1>(a, b, sgn, smem, xs, col0, ncols);
+    dispatch<BMAX, NARROW, B + 1>(a, b, sgn, smem, xs, col0, ncols);
   } else {
     // a width the buffer sizes ruled out: report it, never read past them
     if (threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0) set_status(a.out, CCM_E_INPUT);
@@ -160,7 +175,7 @@ __device__ __forceinline__ void dispatch(const Args& a, int b, int sgn, uint8_t*
 
 // One kernel per width class (widths <= BMAX), so that the register budget
 // of the narrow classes is not set by the 32-bit instances.
-template <int BMAX>
+template <int BMAX, bool NARROW>
 __global__ void __launch_bounds__(256) k_matvec_fast(Args a) {
   extern __shared__ __align__(16) uint8_t smem[];
   if (a.out->status != CCM_OK) return;
@@ -174,13 +189,18 @@ __global__ void __launch_bounds__(256) k_matvec_fast(Args a) {
   int* xs = reinterpret_cast<int*>(smem + a.stage_region);
   for (uint32_t j = threadIdx.x; j < ncols; j += blockDim.x)
     xs[j] = (int)decode_field(a.wx, col0 + j, bx, sx);
-  dispatch<BMAX>(a, b, sgn, smem, xs, col0, ncols);
+  dispatch<BMAX, NARROW>(a, b, sgn, smem, xs, col0, ncols);
 }
 
 // Host launchers, one translation unit per class (matvec_fast{8,16,32}.cu).
-void launch_matvec_fast8(const Args& a, dim3 grid, int threads, size_t smem, cudaStream_t st);
-void launch_matvec_fast16(const Args& a, dim3 grid, int threads, size_t smem, cudaStream_t st);
-void launch_matvec_fast32(const Args& a, dim3 grid, int threads, size_t smem, cudaStream_t st);
+// `narrow`: the width bounds give b_a + b_x + 7 <= 31, so 128 products add up
+// in 32 bits before each int64 flush.
+void launch_matvec_fast8(const Args& a, bool narrow, dim3 grid, int threads, size_t smem,
+                         cudaStream_t st);
+void launch_matvec_fast16(const Args& a, bool narrow, dim3 grid, int threads, size_t smem,
+                          cudaStream_t st);
+void launch_matvec_fast32(const Args& a, bool narrow, dim3 grid, int threads, size_t smem,
+                          cudaStream_t st);
 
 }  // namespace mvf
 }  // namespace ccm

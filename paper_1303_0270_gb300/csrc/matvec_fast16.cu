@@ -6,14 +6,23 @@
 namespace ccm {
 namespace mvf {
 
-void launch_matvec_fast16(const Args& a, dim3 grid, int threads, size_t smem, cudaStream_t st) {
+template <bool NARROW>
+static void launch(const Args& a, dim3 grid, int threads, size_t smem, cudaStream_t st) {
   static bool attr_done = false;
   if (!attr_done) {
-    cudaFuncSetAttribute(k_matvec_fast<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_matvec_fast<16, NARROW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          227 * 1024);
     attr_done = true;
   }
-  k_matvec_fast<16><<<grid, threads, smem, st>>>(a);
+  k_matvec_fast<16, NARROW><<<grid, threads, smem, st>>>(a);
+}
+
+void launch_matvec_fast16(const Args& a, bool narrow, dim3 grid, int threads, size_t smem,
+                         cudaStream_t st) {
+  if (narrow)
+    launch<true>(a, grid, threads, smem, st);
+  else
+    launch<false>(a, grid, threads, smem, st);
 }
 
 }  // namespace mvf

@@ -337,12 +337,13 @@ void run_scale(const ccm_matrix& a, int64_t s, const ccm_matrix& c, cudaStream_t
 }
 
 // Pack an int64 result held in device scratch (matvec / matmul epilogue).
-void run_pack_scratch(const int64_t* vals, const ccm_matrix& out, cudaStream_t st) {
+void run_pack_scratch(const int64_t* vals, const ccm_matrix& out, cudaStream_t st,
+                      bool stats_done) {
   ProdDenseI64 p{vals};
   uint64_t n = out.rows * out.cols;
   const int cls = ew_class(width_bound(out.capacity, n));
   if (cls && n) {
-    launch_stats(p, out.hdr, n, st);
+    if (!stats_done) launch_stats(p, out.hdr, n, st);
     ge::EwCall c{};
     c.kind = ge::EwKind::PackI64;
     c.dense = vals;
@@ -354,7 +355,7 @@ void run_pack_scratch(const int64_t* vals, const ccm_matrix& out, cudaStream_t s
     launch_ew(cls, c, st);
     return;
   }
-  if (n) launch_stats(p, out.hdr, n, st);
+  if (n && !stats_done) launch_stats(p, out.hdr, n, st);
   launch_pack(p, out.hdr, out.words, out.capacity, n, st);
 }
 

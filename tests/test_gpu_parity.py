@@ -285,3 +285,49 @@ def test_matvec_row_aligned(ccm, m, n, ba, bx, sa):
     pa, px = _pack_cap(ccm, a, ba), _pack_cap(ccm, x, bx)
     y = ccm.matvec(pa, px, capacity=ccm.words_for(m, 1, 64))
     assert_same_packed(y, o, f"matvec aligned {m}x{n} b={ba}/{bx}")
+
+
+# ---------------------------------------------------------------------------
+# Tensor-core matmul (exact 4-bit digit decomposition, e4m3 x e4m3 -> f32)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("b", [1, 4, 5, 8, 12, 16])
+@pytest.mark.parametrize("m,k,n", [(128, 128, 128), (300, 520, 200), (129, 1, 257)])
+def test_matmul_tensor_path(ccm, m, k, n, b):
+    a, bm = _rand(m * 7 + b, (m, k), b), _rand(n * 5 + b, (k, n), b)
+    o = oracle.matmul(oracle.pack(a), oracle.pack(bm))
+    pa, pb = _pack_cap(ccm, a, b), _pack_cap(ccm, bm, b)
+    c = ccm.matmul(pa, pb, path=ccm.MATMUL_TENSOR, capacity=ccm.words_for(m, n, 64))
+    assert_same_packed(c, o, f"tensor matmul {m}x{k}x{n} b={b}")
+
+
+def test_matmul_tensor_worst_case_sums(ccm):
+    """Largest digit products in every class: all entries at the extremes of
+    the signed 16-bit range, k = 4096, plus a half-large / half-small row
+    that a narrow accumulator would round."""
+    k = 4096
+    a = np.full((128, k), 32767, dtype=np.int64)
+    a[1::2] = -32768
+    a[2, k // 2:] = 1
+    bm = np.full((k, 64), 32767, dtype=np.int64)
+    bm[:, 1::3] = -32768
+    bm[k // 2:, 2] = 1
+    rows = [0, 1, 2, 3, 127]
+    expect = oracle.matmul_dense(a, bm, rows=rows)
+    pa, pb = _pack_cap(ccm, a, 16), _pack_cap(ccm, bm, 16)
+    c = ccm.matmul(pa, pb, path=ccm.MATMUL_TENSOR, capacity=ccm.words_for(128, 64, 64))
+    got = ccm.unpack(c.check()).cpu().numpy()
+    assert np.array_equal(got[rows], expect)
+
+
+def test_matmul_tensor_and_cudacore_agree(ccm):
+    m, k, n = 384, 1000, 272
+    for b in (4, 8, 13, 16):
+        a, bm = _rand(b, (m, k), b), _rand(b + 1, (k, n), b)
+        pa, pb = _pack_cap(ccm, a, b), _pack_cap(ccm, bm, b)
+        ct = ccm.matmul(pa, pb, path=ccm.MATMUL_TENSOR)
+        cc = ccm.matmul(pa, pb, path=ccm.MATMUL_CUDACORE)
+        assert ct.check().width == cc.check().width
+        assert np.array_equal(words_np(ct), words_np(cc))
+        rows = [0, 191, 383]
+        assert np.array_equal(ccm.unpack(ct).cpu().numpy()[rows],
+                              oracle.matmul_dense(a, bm, rows=rows))
