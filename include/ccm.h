@@ -107,7 +107,7 @@ typedef struct ccm_matrix {
 } ccm_matrix;
 
 /* Operation codes for ccm_workspace_bytes. */
-typedef enum ccm_op { CCM_OP_MATVEC = 1, CCM_OP_MATMUL = 2 } ccm_op;
+typedef enum ccm_op { CCM_OP_MATVEC = 1, CCM_OP_MATMUL = 2, CCM_OP_PACK = 3 } ccm_op;
 
 /* Matmul paths. */
 typedef enum ccm_matmul_path {
@@ -139,9 +139,14 @@ ccm_status ccm_measure(const void* dense, int dtype, uint64_t rows, uint64_t col
  * the dense matrix, then every entry written as a b-bit field at bit e*b of
  * the stream.  `dense` is rows*cols entries of `dtype`, row-major, device.
  * Output in `out` (header + words).  If the exact width needs more than
- * out->capacity words the header gets CCM_E_CAPACITY and no words. */
+ * out->capacity words the header gets CCM_E_CAPACITY and no words.
+ * `ws` (optional, device, 256-byte aligned) of at least
+ * ccm_workspace_bytes(CCM_OP_PACK, rows, cols, out->capacity) bytes lets the
+ * dense input be read once instead of twice (tiles packed at their own width,
+ * then re-coded); NULL or a smaller workspace takes the two-pass route.  The
+ * result is the same either way. */
 ccm_status ccm_pack(const void* dense, int dtype, uint64_t rows, uint64_t cols,
-                    const ccm_matrix* out, ccm_stream_t stream);
+                    const ccm_matrix* out, void* ws, size_t ws_bytes, ccm_stream_t stream);
 
 /* Decompression: every field read back and sign- or zero-extended to
  * `dtype`, row-major into `dense` (rows*cols entries, device).  CCM_I32
@@ -183,7 +188,9 @@ ccm_status ccm_matmul(const ccm_matrix* a, const ccm_matrix* b, const ccm_matrix
                       void* ws, size_t ws_bytes, ccm_stream_t stream);
 
 /* Device workspace needed by `op` on an m x k by k x n problem (matvec: n = 1
- * is the vector, k the inner size). */
+ * is the vector, k the inner size).  An upper bound over all operand widths
+ * (for matmul: the tensor path's digit planes at 4 digits per field).  For
+ * CCM_OP_PACK the arguments are (rows, cols, output capacity in words). */
 size_t ccm_workspace_bytes(int op, uint64_t m, uint64_t k, uint64_t n);
 
 /* Synchronous copy of a device header to host memory (waits for `stream`). */
@@ -202,6 +209,50 @@ ccm_status ccm_gen_uniform(int64_t* out, uint64_t count, uint64_t seed, uint64_t
 ccm_status ccm_gen_poisson(int64_t* out, uint64_t count, uint64_t seed, uint64_t stream_id,
                            uint64_t start, const double* table, uint32_t table_len,
                            ccm_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched matvec: y_i = A_i x_i for many packed matrices of uneven shapes and
+ * widths in one persistent launch (same arithmetic as ccm_matvec, applied to
+ * every entry).  Limits per entry: cols <= 2048 (checked on the host);
+ * width(A) <= 32, width(x) <= 31 and width(A) + width(x) + bitlen(cols) <= 63
+ * so that every sum fits int64 (checked on the GPU: an entry outside them gets
+ * CCM_E_WIDTH in its y header and the other entries are unaffected).
+ *
+ * ccm_batch_plan (synchronous) validates every entry on the host, cuts each
+ * matrix into work units of `unit_segments` row segments (a multiple of 32;
+ * a segment is up to 32 consecutive fields of one row) and writes the plan
+ * (entry descriptors + unit list) to `plan`, a device buffer of at least
+ * ccm_batch_plan_bytes(...) bytes, 256-byte aligned; `info` (host) receives
+ * the counts the launch needs.  The entries' device pointers are baked into
+ * the plan: the buffers must stay where they are while the plan is used.
+ *
+ * ccm_batch_matvec launches an initialisation kernel (validates the headers,
+ * clears y headers and the scratch) and the persistent kernel (`grid` CTAs;
+ * <= 0 picks 4 per SM).  `ws` is device workspace of at least
+ * ccm_batch_workspace_bytes(...) bytes, 256-byte aligned.  Each y_i header
+ * receives its own status.  Both launches are stream-ordered and can be
+ * captured in a CUDA graph. */
+typedef struct ccm_batch_entry {
+  ccm_matrix a; /* m x n */
+  ccm_matrix x; /* n x 1 */
+  ccm_matrix y; /* m x 1 (output) */
+} ccm_batch_entry;
+
+typedef struct ccm_batch_info {
+  uint32_t count;         /* entries */
+  uint32_t units;         /* work units */
+  uint64_t y_rows;        /* sum of the entries' rows */
+  uint32_t unit_segments; /* segments per unit */
+  uint32_t reserved;
+  uint64_t plan_bytes;
+} ccm_batch_info;
+
+size_t ccm_batch_plan_bytes(const ccm_batch_entry* entries, int count, uint32_t unit_segments);
+size_t ccm_batch_workspace_bytes(const ccm_batch_entry* entries, int count);
+ccm_status ccm_batch_plan(const ccm_batch_entry* entries, int count, uint32_t unit_segments,
+                          void* plan, size_t plan_bytes, ccm_batch_info* info);
+ccm_status ccm_batch_matvec(const void* plan, const ccm_batch_info* info, void* ws,
+                            size_t ws_bytes, int grid, ccm_stream_t stream);
 
 /* Runtime instrumentation (no counterpart in the paper).
  * ccm_launch_count: number of kernels this library has launched in this

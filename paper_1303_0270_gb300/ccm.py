@@ -17,7 +17,7 @@ from . import build as _build
 OK, E_INVAL, E_SHAPE, E_WIDTH, E_OVERFLOW, E_CAPACITY, E_RANGE, E_CUDA, E_TIMEOUT, E_INPUT = (
     0, -1, -2, -3, -4, -5, -6, -7, -8, -9)
 I32, I64 = 0, 1
-OP_MATVEC, OP_MATMUL = 1, 2
+OP_MATVEC, OP_MATMUL, OP_PACK = 1, 2, 3
 MATMUL_AUTO, MATMUL_TENSOR, MATMUL_CUDACORE = 0, 1, 2
 MAGIC = 0x314D4343
 HEADER_WORDS = 16  # 64 bytes
@@ -44,6 +44,16 @@ class Matrix(ctypes.Structure):
                 ("cols", ctypes.c_uint64)]
 
 
+class BatchEntry(ctypes.Structure):
+    _fields_ = [("a", Matrix), ("x", Matrix), ("y", Matrix)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint32), ("units", ctypes.c_uint32),
+                ("y_rows", ctypes.c_uint64), ("unit_segments", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("plan_bytes", ctypes.c_uint64)]
+
+
 assert ctypes.sizeof(Header) == 64
 
 _lib = None
@@ -57,7 +67,7 @@ SIGNATURES = {
     "ccm_status_str": ([_i32], ctypes.c_char_p),
     "ccm_version": ([], _i32),
     "ccm_measure": ([_vp, _i32, _u64, _u64, _vp, _vp], _i32),
-    "ccm_pack": ([_vp, _i32, _u64, _u64, _MP, _vp], _i32),
+    "ccm_pack": ([_vp, _i32, _u64, _u64, _MP, _vp, _sz, _vp], _i32),
     "ccm_unpack": ([_MP, _vp, _i32, _vp, _vp], _i32),
     "ccm_get": ([_MP, _vp, _u64, _vp, _vp, _vp], _i32),
     "ccm_add": ([_MP, _MP, _MP, _vp], _i32),
@@ -68,6 +78,11 @@ SIGNATURES = {
     "ccm_header_read": ([_vp, ctypes.POINTER(Header), _vp], _i32),
     "ccm_gen_uniform": ([_vp, _u64, _u64, _u64, _u64, _i64, _i64, _vp], _i32),
     "ccm_gen_poisson": ([_vp, _u64, _u64, _u64, _u64, _vp, ctypes.c_uint32, _vp], _i32),
+    "ccm_batch_plan_bytes": ([ctypes.POINTER(BatchEntry), _i32, ctypes.c_uint32], _sz),
+    "ccm_batch_workspace_bytes": ([ctypes.POINTER(BatchEntry), _i32], _sz),
+    "ccm_batch_plan": ([ctypes.POINTER(BatchEntry), _i32, ctypes.c_uint32, _vp, _sz,
+                        ctypes.POINTER(BatchInfo)], _i32),
+    "ccm_batch_matvec": ([_vp, ctypes.POINTER(BatchInfo), _vp, _sz, _i32, _vp], _i32),
     "ccm_launch_count": ([], _u64),
     "ccm_profile_next": ([_vp, _vp], _i32),
 }
@@ -224,12 +239,18 @@ def measure(t: torch.Tensor, stream=None) -> tuple[int, int]:
     return h.width, h.is_signed
 
 
-def pack_into(t: torch.Tensor, out: PackedMatrix, stream=None) -> PackedMatrix:
-    """Asynchronous SM pack of a dense CUDA tensor into a preallocated matrix."""
+def pack_into(t: torch.Tensor, out: PackedMatrix, stream=None, ws: torch.Tensor | None = None,
+              single_pass: bool = True) -> PackedMatrix:
+    """Asynchronous SM pack of a dense CUDA tensor into a preallocated matrix
+    (single pass over the dense data when a workspace applies)."""
     t, rows, cols, dt = _as_dense(t)
     m = out.c()
+    if ws is None and single_pass:
+        nb = workspace_bytes(OP_PACK, rows, cols, out.capacity)
+        ws = torch.empty(nb, dtype=torch.uint8, device=t.device) if nb else None
+    wsp = ctypes.c_void_p(ws.data_ptr()) if ws is not None else None
     _check(lib().ccm_pack(ctypes.c_void_p(t.data_ptr()), dt, rows, cols, ctypes.byref(m),
-                          _stream(stream)), "ccm_pack")
+                          wsp, ws.numel() if ws is not None else 0, _stream(stream)), "ccm_pack")
     out._written()
     return out
 

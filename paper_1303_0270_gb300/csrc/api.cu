@@ -72,12 +72,13 @@ ccm_status ccm_measure(const void* dense, int dtype, uint64_t rows, uint64_t col
 }
 
 ccm_status ccm_pack(const void* dense, int dtype, uint64_t rows, uint64_t cols,
-                    const ccm_matrix* out, ccm_stream_t stream) {
+                    const ccm_matrix* out, void* ws, size_t ws_bytes, ccm_stream_t stream) {
   if (!valid_out(out) || (rows * cols && !dense)) return CCM_E_INVAL;
   if (dtype != CCM_I32 && dtype != CCM_I64) return CCM_E_INVAL;
   if (out->rows != rows || out->cols != cols) return CCM_E_SHAPE;
   if (!capacity_ok(out)) return CCM_E_CAPACITY;
-  ccm::run_pack(dense, dtype, rows, cols, *out, to_cuda(stream));
+  if (ws && reinterpret_cast<uintptr_t>(ws) % 256) return CCM_E_INVAL;
+  ccm::run_pack(dense, dtype, rows, cols, *out, ws, ws_bytes, to_cuda(stream));
   return launched();
 }
 
@@ -118,13 +119,8 @@ ccm_status ccm_scale(const ccm_matrix* a, int64_t s, const ccm_matrix* c, ccm_st
 size_t ccm_workspace_bytes(int op, uint64_t m, uint64_t k, uint64_t n) {
   switch (op) {
     case CCM_OP_MATVEC: return ccm::matvec_workspace(m, k);
-    case CCM_OP_MATMUL: {
-      // the tensor path's digit planes depend on the operand widths, which a
-      // shape-only query cannot see: size for the widest it accepts (16 bits)
-      ccm_matrix a{nullptr, nullptr, ccm::words_for(m * k, 16), m, k};
-      ccm_matrix b{nullptr, nullptr, ccm::words_for(k * n, 16), k, n};
-      return ccm::matmul_workspace(a, b);
-    }
+    case CCM_OP_PACK: return ccm::pack_workspace(m, k, n);
+    case CCM_OP_MATMUL: return ccm::matmul_workspace_upper(m, k, n);
     default: return 0;
   }
 }
@@ -149,7 +145,7 @@ ccm_status ccm_matmul(const ccm_matrix* a, const ccm_matrix* b, const ccm_matrix
   if (reinterpret_cast<uintptr_t>(ws) % 256) return CCM_E_INVAL;
   if (b->rows != a->cols || c->rows != a->rows || c->cols != b->cols) return CCM_E_SHAPE;
   if (!capacity_ok(c)) return CCM_E_CAPACITY;
-  if (ws_bytes < ccm::matmul_workspace(*a, *b)) return CCM_E_CAPACITY;
+  if (ws_bytes < ccm::matmul_workspace(*a, *b)) return CCM_E_CAPACITY;  // <= the shape bound
   int st = ccm::run_matmul(*a, *b, *c, path, ws, to_cuda(stream));
   if (st != CCM_OK) return (ccm_status)st;
   return launched();

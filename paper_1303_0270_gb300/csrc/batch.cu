@@ -1,0 +1,437 @@
+// batch.cu -- y_i = A_i x_i for thousands of packed matrices of uneven
+// shapes and widths in one persistent launch.
+//
+// Work unit: a run of consecutive 32-field row segments of one matrix.  Row i
+// of an m x n matrix is cut into ceil(n / 32) segments of up to 32 fields; a
+// lane owns one segment.  A segment starts at an arbitrary bit, so the lane
+// loads the b + 1 words that cover it, funnel-shifts them once to the
+// segment's start and then decodes its fields with shifts fixed at compile
+// time (the width is dispatched per unit on the GPU).  x is decoded once per
+// unit into shared memory in a [f/4][segment][f%4] layout, so the four x
+// values a lane needs next are one conflict-free 16-byte load.  Lanes of a
+// warp hold consecutive segments; a segmented shuffle reduction keyed by row
+// leaves each row's partial sum in its first lane, which adds it to the int64
+// y scratch with one atomic.
+//
+// Persistent CTAs take units from an atomic ticket.  The CTA that finishes
+// the last unit of a matrix (per-matrix completion counter) re-packs that
+// matrix's y at its exact width (width rule of Eq. 1 with the two's
+// complement reading) and writes y's header -- so the whole batch is one
+// launch after a small initialisation kernel, and both can be captured in a
+// CUDA graph.
+#include <cstring>
+#include <vector>
+
+#include "ccm_device.cuh"
+#include "kernels.h"
+
+namespace ccm {
+namespace bt {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxCols = 2048;      // x of at most 2048 entries per matrix
+constexpr int kWordsPerWarp = 32 * 32 + 64;  // staging for 32 segments of width <= 32
+
+struct Mat {
+  const ccm_header* ha;
+  const uint32_t* wa;
+  const ccm_header* hx;
+  const uint32_t* wx;
+  ccm_header* hy;
+  uint32_t* wy;
+  uint64_t a_cap, x_cap, y_cap;
+  uint32_t m, n;
+  uint64_t y_off;      // offset of this matrix's rows in the int64 y scratch
+  uint32_t units;      // work units of this matrix
+  uint32_t pad;
+};
+
+struct Unit {
+  uint32_t mat;
+  uint32_t seg0;   // first segment (row-major numbering within the matrix)
+  uint32_t nseg;   // number of segments
+  uint32_t pad;
+};
+
+struct Args {
+  const Mat* mats;
+  const Unit* units;
+  uint32_t nmats, nunits;
+  int64_t* yscratch;
+  uint32_t* ticket;     // unit dispenser
+  uint32_t* done;       // per-matrix completed units
+};
+
+__device__ __forceinline__ int stage_pos(int w, int b) { return (b & 1) ? w : w + (w >> 5); }
+
+// ---------------------------------------------------------------------------
+// Initialisation: validate inputs, write y headers, clear counters and the
+// y scratch.
+// ---------------------------------------------------------------------------
+__global__ void k_batch_init(Args a, uint64_t yrows) {
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = tid; i < yrows; i += stride) a.yscratch[i] = 0;
+  for (uint64_t i = tid; i < a.nmats; i += stride) {
+    const Mat& M = a.mats[i];
+    int st = check_input(M.ha, M.m, M.n, M.a_cap);
+    if (st == CCM_OK) st = check_input(M.hx, M.n, 1, M.x_cap);
+    // widths the kernel handles, and sums that provably fit int64
+    if (st == CCM_OK && (M.ha->width > 32 || M.hx->width > 31 ||
+                         M.ha->width + M.hx->width + bitlen64(M.n) > 63))
+      st = CCM_E_WIDTH;
+    ccm_header* y = M.hy;
+    y->magic = CCM_MAGIC;
+    y->width = 0;
+    y->is_signed = 0;
+    y->status = st;
+    y->rows = M.m;
+    y->cols = 1;
+    y->nwords = 0;
+    y->stat_or = 0;
+    y->stat_neg = 0;
+    a.done[i] = 0;
+  }
+  if (tid == 0) *a.ticket = 0;
+}
+
+// ---------------------------------------------------------------------------
+// One unit at compile-time width B.
+// ---------------------------------------------------------------------------
+template <int B, bool SGN>
+__device__ __noinline__ void run_unit(const Mat& M, const Unit& u, const int4* __restrict__ x4,
+                                      uint32_t nseg_row, uint32_t* stage, int64_t* ys) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const uint32_t n = M.n;
+  for (uint32_t base = warp * 32; base < u.nseg; base += kWarps * 32) {
+    // the warp's 32 consecutive segments
+    const uint32_t id = u.seg0 + base + lane;
+    const bool live = base + lane < u.nseg;
+    const uint32_t row = live ? id / nseg_row : 0xffffffffu;
+    const uint32_t s = live ? id % nseg_row : 0;
+    const uint32_t col0 = 32 * s;
+    const uint32_t nf = live ? min(32u, n - col0) : 0;
+    const uint64_t bit = ((uint64_t)row * n + col0) * B;
+    // words of all 32 segments: from the first segment's first word
+    const uint32_t first_id = u.seg0 + base;
+    const uint32_t frow = first_id / nseg_row, fs = first_id % nseg_row;
+    const uint64_t w_first = (((uint64_t)frow * n + 32 * fs) * B) >> 5;
+    const uint32_t last = min(base + 32, u.nseg) - 1 + u.seg0;
+    const uint32_t lrow = last / nseg_row, ls = last % nseg_row;
+    const uint64_t end_bit = ((uint64_t)lrow * n + min(n, 32 * ls + 32)) * B;
+    const uint32_t nwords = (uint32_t)(((end_bit + 31) >> 5) - w_first) + 1;
+    const uint64_t dw = data_words((uint64_t)M.m * n, B);
+    for (uint32_t w = lane; w < nwords; w += 32) {
+      const uint64_t g = w_first + w;
+      stage[stage_pos((int)w, B)] = g < dw ? __ldg(M.wa + g) : 0u;
+    }
+    __syncwarp();
+    long long acc = 0;
+    if (live) {
+      const int wo = (int)((bit >> 5) - w_first), s0 = (int)(bit & 31);
+      uint32_t w[B + 1];
+#pragma unroll
+      for (int j = 0; j <= B; ++j) w[j] = stage[stage_pos(wo + j, B)];
+#pragma unroll
+      for (int j = 0; j < B; ++j) w[j] = __funnelshift_r(w[j], w[j + 1], s0);
+      const int4* xv = x4 + s;  // [f/4][segment] of int4
+#pragma unroll
+      for (int f4 = 0; f4 < 8; ++f4) {
+        const int4 xq = xv[f4 * nseg_row];
+        const int xa[4] = {xq.x, xq.y, xq.z, xq.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int f = 4 * f4 + q;
+          const int b0 = f * B, wi = b0 >> 5, sh = b0 & 31;
+          uint32_t t = (sh + B <= 32) ? (w[wi] >> sh) : __funnelshift_r(w[wi], w[wi + 1], sh);
+          long long v;
+          if constexpr (B == 32)
+            v = SGN ? (long long)(int)t : (long long)t;
+          else if constexpr (SGN)
+            v = (int)(t << (32 - B)) >> (32 - B);
+          else
+            v = t & ((1u << B) - 1u);
+          if (f < (int)nf) acc += v * xa[q];
+        }
+      }
+    }
+    __syncwarp();
+    // segmented reduction by row: the first lane of each row gets the total
+    uint32_t r = row;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const long long o = __shfl_down_sync(0xffffffffu, acc, d);
+      const uint32_t ro = __shfl_down_sync(0xffffffffu, r, d);
+      if (lane + d < 32 && ro == r) acc += o;
+    }
+    const uint32_t rprev = __shfl_up_sync(0xffffffffu, r, 1);
+    if (live && (lane == 0 || rprev != r))
+      atomicAdd(reinterpret_cast<unsigned long long*>(ys + row), (unsigned long long)acc);
+  }
+}
+
+// Re-pack y of one matrix (m <= 2^31 values in scratch) at its exact width;
+// the whole CTA takes part.
+__device__ void pack_y(const Mat& M, const int64_t* __restrict__ ys, uint64_t* s_or,
+                       uint32_t* s_neg) {
+  const uint32_t m = M.m;
+  uint64_t orv = 0;
+  uint32_t neg = 0;
+  for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+    const int64_t v = __ldcg(ys + i);
+    orv |= fold(v);
+    neg |= (uint32_t)(v < 0);
+  }
+  orv = warp_or64(orv);
+  neg = __reduce_or_sync(0xffffffffu, neg);
+  if (threadIdx.x % 32 == 0) {
+    s_or[threadIdx.x / 32] = orv;
+    s_neg[threadIdx.x / 32] = neg;
+  }
+  __syncthreads();
+  orv = 0;
+  neg = 0;
+  for (int k = 0; k < kWarps; ++k) {
+    orv |= s_or[k];
+    neg |= s_neg[k];
+  }
+  const int b = width_from_stats(orv, neg);
+  const uint64_t nw = words_for(m, b), dw = data_words(m, b);
+  const bool fits = nw <= M.y_cap;
+  if (threadIdx.x == 0) {
+    ccm_header* h = M.hy;
+    h->stat_or = orv;
+    h->stat_neg = neg;
+    h->width = b;
+    h->is_signed = neg ? 1 : 0;
+    h->nwords = nw;
+    if (!fits) h->status = CCM_E_CAPACITY;
+  }
+  if (!fits) return;
+  const uint64_t mask = field_mask(b);
+  for (uint64_t w = threadIdx.x; w < nw; w += blockDim.x) {
+    uint32_t acc = 0;
+    if (w < dw) {
+      const uint64_t bit0 = w * 32;
+      uint64_t f = bit0 / b;
+      const uint64_t f_end = min((bit0 + 31) / b, (uint64_t)m - 1);
+      for (; f <= f_end; ++f) {
+        const uint64_t pat = (uint64_t)__ldcg(ys + f) & mask;
+        const int64_t o = (int64_t)(f * b) - (int64_t)bit0;
+        acc |= o >= 0 ? (uint32_t)(pat << o) : (uint32_t)(pat >> (-o));
+      }
+    }
+    M.wy[w] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_batch_mv(Args a) {
+  __shared__ __align__(16) int4 s_x4[kMaxCols / 4];
+  __shared__ uint32_t s_stage[kWarps][kWordsPerWarp];
+  __shared__ uint32_t s_unit;
+  __shared__ int s_last;
+  __shared__ uint64_t s_or[kWarps];
+  __shared__ uint32_t s_neg[kWarps];
+  uint32_t cached = 0xffffffffu;  // matrix whose x is in shared memory
+  for (;;) {
+    if (threadIdx.x == 0) s_unit = atomicAdd(a.ticket, 1u);
+    __syncthreads();
+    const uint32_t ui = s_unit;
+    if (ui >= a.nunits) break;
+    const Unit u = a.units[ui];
+    const Mat& M = a.mats[u.mat];
+    const bool ok = M.hy->status == CCM_OK;  // validated by k_batch_init
+    const uint32_t nseg_row = (M.n + 31) / 32;
+    if (ok) {
+      if (cached != u.mat) {
+        // x -> shared, layout [f/4][segment][f%4]
+        const int bx = M.hx->width, sx = M.hx->is_signed;
+        int* xs = reinterpret_cast<int*>(s_x4);
+        for (uint32_t j = threadIdx.x; j < nseg_row * 32; j += blockDim.x) {
+          const uint32_t seg = j / 32, f = j % 32;
+          const int v = j < M.n ? (int)decode_field(M.wx, j, bx, sx) : 0;
+          xs[((f / 4) * nseg_row + seg) * 4 + (f % 4)] = v;
+        }
+        cached = u.mat;
+      }
+      __syncthreads();
+      const int b = M.ha->width, sgn = M.ha->is_signed;
+      int64_t* ys = a.yscratch + M.y_off;
+      uint32_t* stage = s_stage[threadIdx.x / 32];
+      switch (2 * b + sgn) {
+#define CCM_BT_CASE(B)                                                     \
+  case 2 * B: run_unit<B, false>(M, u, s_x4, nseg_row, stage, ys); break; \
+  case 2 * B + 1: run_unit<B, true>(M, u, s_x4, nseg_row, stage, ys); break;
+        CCM_BT_CASE(1) CCM_BT_CASE(2) CCM_BT_CASE(3) CCM_BT_CASE(4) CCM_BT_CASE(5)
+        CCM_BT_CASE(6) CCM_BT_CASE(7) CCM_BT_CASE(8) CCM_BT_CASE(9) CCM_BT_CASE(10)
+        CCM_BT_CASE(11) CCM_BT_CASE(12) CCM_BT_CASE(13) CCM_BT_CASE(14) CCM_BT_CASE(15)
+        CCM_BT_CASE(16) CCM_BT_CASE(17) CCM_BT_CASE(18) CCM_BT_CASE(19) CCM_BT_CASE(20)
+        CCM_BT_CASE(21) CCM_BT_CASE(22) CCM_BT_CASE(23) CCM_BT_CASE(24) CCM_BT_CASE(25)
+        CCM_BT_CASE(26) CCM_BT_CASE(27) CCM_BT_CASE(28) CCM_BT_CASE(29) CCM_BT_CASE(30)
+        CCM_BT_CASE(31) CCM_BT_CASE(32)
+#undef CCM_BT_CASE
+        default: break;
+      }
+    }
+    // completion of the unit; the CTA that completes a matrix packs its y
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(a.done + u.mat, 1u) + 1 == M.units;
+    __syncthreads();
+    if (s_last && ok) {
+      __threadfence();
+      pack_y(M, a.yscratch + M.y_off, s_or, s_neg);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace bt
+}  // namespace ccm
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+namespace ccm {
+namespace bt {
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct Layout {
+  uint32_t nmats = 0, nunits = 0;
+  uint64_t yrows = 0;
+  size_t mats_off = 0, units_off = 0, bytes = 0;
+};
+
+uint64_t segments_of(const ccm_batch_entry& e) { return e.a.rows * ((e.a.cols + 31) / 32); }
+
+int validate(const ccm_batch_entry& e) {
+  const ccm_matrix &a = e.a, &x = e.x, &y = e.y;
+  if (!a.hdr || !x.hdr || !y.hdr) return CCM_E_INVAL;
+  if (x.rows != a.cols || x.cols != 1 || y.rows != a.rows || y.cols != 1) return CCM_E_SHAPE;
+  if (a.cols > (uint64_t)kMaxCols || a.rows >= (1ull << 31)) return CCM_E_SHAPE;
+  const uint64_t n = a.rows * a.cols;
+  if (y.capacity < words_for(y.rows, 1)) return CCM_E_CAPACITY;
+  auto al = [](const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
+  if (!al(a.hdr) || !al(x.hdr) || !al(y.hdr) || !al(a.words) || !al(x.words) || !al(y.words))
+    return CCM_E_INVAL;
+  if ((n && !a.words) || (a.cols && !x.words) || (y.capacity && !y.words)) return CCM_E_INVAL;
+  return CCM_OK;
+}
+
+Layout layout(const ccm_batch_entry* e, int count, uint32_t unit_segs) {
+  Layout L;
+  L.nmats = (uint32_t)count;
+  uint64_t units = 0;
+  for (int i = 0; i < count; ++i) {
+    const uint64_t s = segments_of(e[i]);
+    units += s ? (s + unit_segs - 1) / unit_segs : 1;
+    L.yrows += e[i].a.rows;
+  }
+  L.nunits = (uint32_t)units;
+  L.mats_off = align256(sizeof(ccm_batch_info));
+  L.units_off = L.mats_off + align256(sizeof(Mat) * (size_t)count);
+  L.bytes = L.units_off + align256(sizeof(Unit) * (size_t)units);
+  return L;
+}
+
+}  // namespace bt
+}  // namespace ccm
+
+extern "C" {
+
+size_t ccm_batch_plan_bytes(const ccm_batch_entry* entries, int count, uint32_t unit_segments) {
+  if (!entries || count <= 0 || unit_segments == 0) return 0;
+  return ccm::bt::layout(entries, count, unit_segments).bytes;
+}
+
+size_t ccm_batch_workspace_bytes(const ccm_batch_entry* entries, int count) {
+  if (!entries || count <= 0) return 0;
+  uint64_t yrows = 0;
+  for (int i = 0; i < count; ++i) yrows += entries[i].a.rows;
+  return ccm::bt::align256(yrows * 8) + ccm::bt::align256((size_t)count * 4) + 256;
+}
+
+ccm_status ccm_batch_plan(const ccm_batch_entry* entries, int count, uint32_t unit_segments,
+                          void* plan, size_t plan_bytes, ccm_batch_info* info) {
+  using namespace ccm::bt;
+  if (!entries || count <= 0 || !plan || !info || unit_segments == 0) return CCM_E_INVAL;
+  if (unit_segments % 32) return CCM_E_INVAL;
+  for (int i = 0; i < count; ++i) {
+    int st = validate(entries[i]);
+    if (st != CCM_OK) return (ccm_status)st;
+  }
+  Layout L = layout(entries, count, unit_segments);
+  if (plan_bytes < L.bytes || reinterpret_cast<uintptr_t>(plan) % 256) return CCM_E_CAPACITY;
+  std::vector<uint8_t> host(L.bytes, 0);
+  Mat* mats = reinterpret_cast<Mat*>(host.data() + L.mats_off);
+  Unit* units = reinterpret_cast<Unit*>(host.data() + L.units_off);
+  uint64_t yoff = 0, u = 0;
+  for (int i = 0; i < count; ++i) {
+    const ccm_batch_entry& e = entries[i];
+    Mat& M = mats[i];
+    M.ha = e.a.hdr;
+    M.wa = e.a.words;
+    M.hx = e.x.hdr;
+    M.wx = e.x.words;
+    M.hy = e.y.hdr;
+    M.wy = e.y.words;
+    M.a_cap = e.a.capacity;
+    M.x_cap = e.x.capacity;
+    M.y_cap = e.y.capacity;
+    M.m = (uint32_t)e.a.rows;
+    M.n = (uint32_t)e.a.cols;
+    M.y_off = yoff;
+    yoff += e.a.rows;
+    const uint64_t s = segments_of(e);
+    const uint64_t nu = s ? (s + unit_segments - 1) / unit_segments : 1;
+    M.units = (uint32_t)nu;
+    for (uint64_t k = 0; k < nu; ++k, ++u) {
+      units[u].mat = (uint32_t)i;
+      units[u].seg0 = (uint32_t)(k * unit_segments);
+      units[u].nseg = (uint32_t)(s ? ccm::umin(unit_segments, s - k * unit_segments) : 0);
+    }
+  }
+  info->count = (uint32_t)count;
+  info->units = L.nunits;
+  info->y_rows = L.yrows;
+  info->unit_segments = unit_segments;
+  info->plan_bytes = L.bytes;
+  std::memcpy(host.data(), info, sizeof(ccm_batch_info));
+  if (cudaMemcpy(plan, host.data(), L.bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+    return CCM_E_CUDA;
+  return CCM_OK;
+}
+
+ccm_status ccm_batch_matvec(const void* plan, const ccm_batch_info* info, void* ws,
+                            size_t ws_bytes, int grid, ccm_stream_t stream) {
+  using namespace ccm::bt;
+  if (!plan || !info || !ws || info->count == 0) return CCM_E_INVAL;
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return CCM_E_INVAL;
+  const size_t need = align256(info->y_rows * 8) + align256((size_t)info->count * 4) + 256;
+  if (ws_bytes < need) return CCM_E_CAPACITY;
+  Layout L;
+  L.mats_off = align256(sizeof(ccm_batch_info));
+  L.units_off = L.mats_off + align256(sizeof(Mat) * (size_t)info->count);
+  Args a;
+  a.mats = reinterpret_cast<const Mat*>((const uint8_t*)plan + L.mats_off);
+  a.units = reinterpret_cast<const Unit*>((const uint8_t*)plan + L.units_off);
+  a.nmats = info->count;
+  a.nunits = info->units;
+  a.yscratch = (int64_t*)ws;
+  a.done = (uint32_t*)((uint8_t*)ws + align256(info->y_rows * 8));
+  a.ticket = (uint32_t*)((uint8_t*)ws + align256(info->y_rows * 8) + align256((size_t)info->count * 4));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const uint64_t init_items = ccm::umax(info->y_rows, info->count);
+  int gi = (int)ccm::umin((init_items + 255) / 256, (uint64_t)ccm::num_sms() * 8);
+  k_batch_init<<<gi < 1 ? 1 : gi, 256, 0, st>>>(a, info->y_rows);
+  if (grid <= 0) grid = ccm::num_sms() * 4;
+  ccm::profile_begin(st);
+  k_batch_mv<<<grid, kThreads, 0, st>>>(a);
+  ccm::profile_end(st);
+  ccm::note_launch(2);
+  return cudaGetLastError() == cudaSuccess ? CCM_OK : CCM_E_CUDA;
+}
+
+}  // extern "C"

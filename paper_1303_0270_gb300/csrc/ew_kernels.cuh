@@ -252,6 +252,114 @@ __global__ void __launch_bounds__(kThreads) k_pack_dense(const T* __restrict__ s
   }
 }
 
+// ---------------------------------------------------------------------------
+// Single-pass pack of a dense matrix (with workspace).  k_pack_local reads
+// every dense tile once: it takes the tile's own width b_loc (the width rule
+// on the tile's 1024 values), packs the tile at b_loc into its workspace slot
+// (32*BMAX words) and merges the tile statistics into the output header.
+// Since the matrix width is the largest tile width, b_loc <= b and every
+// slot fits.  k_repack then re-codes each slot from b_loc to b (packed bytes
+// only, mostly from L2).  Dense traffic: one read instead of two.
+// ---------------------------------------------------------------------------
+template <typename T, int BMAX>
+__global__ void __launch_bounds__(kThreads) k_pack_local(const T* __restrict__ src,
+                                                         ccm_header* out,
+                                                         uint32_t* __restrict__ slots,
+                                                         uint8_t* __restrict__ tile_width,
+                                                         uint64_t n) {
+  __shared__ __align__(16) uint32_t s_buf[kWarps][kBufWords];
+  if (out->status != CCM_OK) return;
+  const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+  uint32_t* buf = s_buf[warp];
+  T* tb = reinterpret_cast<T*>(buf);
+  const uint64_t ntiles = (n + kTile - 1) / kTile;
+  const uint64_t gwarps = (uint64_t)gridDim.x * kWarps;
+  uint64_t g_or = 0;
+  uint32_t g_neg = 0;
+  for (uint64_t tile = (uint64_t)blockIdx.x * kWarps + warp; tile < ntiles; tile += gwarps) {
+    const uint32_t nt = (uint32_t)umin((uint64_t)kTile, n - tile * kTile);
+    stage_dense<T>(tb, src, tile * kTile, nt, lane);
+    __syncwarp();
+    int64_t v[32];
+    uint64_t orv = 0;
+    uint32_t neg = 0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      v[k] = (int64_t)tb[33 * lane + k];
+      orv |= fold(v[k]);
+      neg |= (uint32_t)(v[k] < 0);
+    }
+    __syncwarp();
+    orv = warp_or64(orv);
+    neg = __reduce_or_sync(0xffffffffu, neg);
+    g_or |= orv;
+    g_neg |= neg;
+    const int bl = width_from_stats(orv, neg);
+    if (bl <= BMAX) {
+      uint32_t u[32];
+      const uint32_t mask = bl >= 32 ? 0xffffffffu : ((1u << bl) - 1u);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) u[k] = (uint32_t)v[k] & mask;
+      encode_dispatch<BMAX>(bl, u, buf, lane);
+      __syncwarp();
+      uint4* dst = reinterpret_cast<uint4*>(slots + tile * (uint64_t)(32 * BMAX));
+      for (int q = lane; q < 8 * bl; q += 32) {
+        const int w = 4 * q;
+        dst[q] = make_uint4(buf[stage_pos(w, bl)], buf[stage_pos(w + 1, bl)],
+                            buf[stage_pos(w + 2, bl)], buf[stage_pos(w + 3, bl)]);
+      }
+      __syncwarp();
+    }
+    if (lane == 0) tile_width[tile] = bl <= BMAX ? (uint8_t)(bl | (neg ? 0x80 : 0)) : 0xFF;
+  }
+  if (lane == 0) {
+    if (g_or) atomicOr(reinterpret_cast<unsigned long long*>(&out->stat_or), (unsigned long long)g_or);
+    if (g_neg) atomicOr(&out->stat_neg, 1u);
+  }
+}
+
+template <int BMAX>
+__global__ void __launch_bounds__(kThreads) k_repack(const uint32_t* __restrict__ slots,
+                                                     const uint8_t* __restrict__ tile_width,
+                                                     ccm_header* out, uint32_t* words,
+                                                     uint64_t capacity, uint64_t n) {
+  __shared__ __align__(16) uint32_t s_buf[kWarps][kBufWords];
+  int b, sgn;
+  if (!resolve_output(out, words, capacity, n, b, sgn)) return;  // also: a tile wider than BMAX
+  const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+  uint32_t* buf = s_buf[warp];
+  const uint64_t dw = data_words(n, b);
+  const uint32_t mask = b >= 32 ? 0xffffffffu : ((1u << b) - 1u);
+  const uint64_t ntiles = (n + kTile - 1) / kTile;
+  const uint64_t gwarps = (uint64_t)gridDim.x * kWarps;
+  for (uint64_t tile = (uint64_t)blockIdx.x * kWarps + warp; tile < ntiles; tile += gwarps) {
+    const int tw = tile_width[tile];
+    const int bl = tw & 0x7f, sl = tw >> 7;
+    const uint4* src = reinterpret_cast<const uint4*>(slots + tile * (uint64_t)(32 * BMAX));
+    for (int q = lane; q < 8 * bl; q += 32) {
+      const uint4 v = __ldg(src + q);
+      const int w = 4 * q;
+      buf[stage_pos(w, bl)] = v.x;
+      buf[stage_pos(w + 1, bl)] = v.y;
+      buf[stage_pos(w + 2, bl)] = v.z;
+      buf[stage_pos(w + 3, bl)] = v.w;
+    }
+    __syncwarp();
+    uint32_t u[32];
+    decode_dispatch<BMAX>(bl, sl, buf, lane, [&](int k, int64_t x) { u[k] = (uint32_t)x & mask; });
+    __syncwarp();
+    encode_dispatch<BMAX>(b, u, buf, lane);
+    __syncwarp();
+    store_packed(buf, words, tile, b, dw, lane);
+    __syncwarp();
+  }
+}
+
+inline size_t pack_ws_bytes(uint64_t n, int cls) {
+  const uint64_t ntiles = (n + kTile - 1) / kTile;
+  return ((ntiles * 32 * cls * 4 + 255) & ~(size_t)255) + ((ntiles + 255) & ~(size_t)255);
+}
+
 // Unpack: decode every group and write the values densely (int64 or int32).
 template <typename T, int BMAX>
 __global__ void __launch_bounds__(kThreads) k_unpack_ge(const ccm_header* h,
@@ -288,7 +396,10 @@ __global__ void __launch_bounds__(kThreads) k_unpack_ge(const ccm_header* h,
 }
 
 // What the host asks one class to run.
-enum class EwKind { PackI64, PackI32, AddStats, AddPack, ScaleStats, ScalePack, UnpackI64, UnpackI32 };
+enum class EwKind {
+  PackI64, PackI32, AddStats, AddPack, ScaleStats, ScalePack, UnpackI64, UnpackI32,
+  LocalI64, LocalI32, Repack
+};
 
 struct EwCall {
   EwKind kind;
@@ -303,6 +414,7 @@ struct EwCall {
   uint64_t capacity;
   uint64_t rows, cols;
   int32_t* err;           // unpack status
+  void* ws;               // Local* / Repack: workspace (slots, then tile widths)
 };
 
 inline int ew_grid(uint64_t n, int per_sm) {
@@ -348,6 +460,23 @@ void launch_ew_class(const EwCall& c, cudaStream_t st) {
         k_ew<OpScale<false>, C, true><<<g, kThreads, 0, st>>>(OpScale<false>{a, c.s}, c.out,
                                                                c.words, c.capacity, n);
       break;
+    case EwKind::LocalI64:
+    case EwKind::LocalI32:
+    case EwKind::Repack: {
+      const uint64_t ntiles = (n + kTile - 1) / kTile;
+      uint32_t* slots = (uint32_t*)c.ws;
+      uint8_t* widths = (uint8_t*)c.ws + ((ntiles * 32 * C * 4 + 255) & ~(size_t)255);
+      const int gl = ew_grid(n, 12);
+      if (c.kind == EwKind::LocalI64)
+        k_pack_local<int64_t, C><<<gl, kThreads, 0, st>>>((const int64_t*)c.dense, c.out, slots,
+                                                          widths, n);
+      else if (c.kind == EwKind::LocalI32)
+        k_pack_local<int32_t, C><<<gl, kThreads, 0, st>>>((const int32_t*)c.dense, c.out, slots,
+                                                          widths, n);
+      else
+        k_repack<C><<<gl, kThreads, 0, st>>>(slots, widths, c.out, c.words, c.capacity, n);
+      break;
+    }
     case EwKind::UnpackI64:
       k_unpack_ge<int64_t, C><<<ew_grid(n, 12), kThreads, 0, st>>>(
           c.out, c.words, c.rows, c.cols, c.capacity, (int64_t*)c.dense, c.err);

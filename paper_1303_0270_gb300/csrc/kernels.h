@@ -21,8 +21,10 @@ void profile_end(cudaStream_t st);
 
 void run_measure(const void* dense, int dtype, uint64_t rows, uint64_t cols, ccm_header* hdr,
                  cudaStream_t st);
+// Workspace of the single-pass pack (0 when the capacity gives no width class).
+size_t pack_workspace(uint64_t rows, uint64_t cols, uint64_t capacity);
 void run_pack(const void* dense, int dtype, uint64_t rows, uint64_t cols, const ccm_matrix& out,
-              cudaStream_t st);
+              void* ws, size_t ws_bytes, cudaStream_t st);
 void run_unpack(const ccm_matrix& a, void* dense, int dtype, int32_t* err, cudaStream_t st);
 void run_get(const ccm_matrix& a, const uint64_t* idx, uint64_t count, int64_t* out, int32_t* err,
              cudaStream_t st);
@@ -38,6 +40,9 @@ void run_matvec(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& y, v
                 cudaStream_t st);
 
 size_t matmul_workspace(const ccm_matrix& a, const ccm_matrix& b);
+// Shape-only bound on matmul_workspace (the widths are unknown): the tensor
+// path at its widest (4 digits per field).
+size_t matmul_workspace_upper(uint64_t m, uint64_t k, uint64_t n);
 int run_matmul(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, int path, void* ws,
                cudaStream_t st);
 

@@ -104,6 +104,11 @@ size_t matmul_workspace(const ccm_matrix& a, const ccm_matrix& b) {
   return c_bytes + matmul_tc_workspace(a, b) + 256;
 }
 
+size_t matmul_workspace_upper(uint64_t m, uint64_t k, uint64_t n) {
+  size_t c_bytes = ((m * n * sizeof(int64_t)) + 255) & ~(size_t)255;
+  return c_bytes + matmul_tc_workspace_upper(m, k, n) + 256;
+}
+
 int run_matmul(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, int path, void* ws,
                cudaStream_t st) {
   const uint64_t m = a.rows, k = a.cols, n = b.cols;

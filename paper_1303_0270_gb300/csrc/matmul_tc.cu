@@ -496,6 +496,12 @@ size_t matmul_tc_workspace(const ccm_matrix& a, const ccm_matrix& b) {
   return tc::round_up(p.a_bytes, 256) + tc::round_up(p.b_bytes, 256);
 }
 
+size_t matmul_tc_workspace_upper(uint64_t m, uint64_t k, uint64_t n) {
+  if (!m || !n || !k) return 0;
+  tc::Plan p = tc::plan_for(m, k, n, 4);
+  return tc::round_up(p.a_bytes, 256) + tc::round_up(p.b_bytes, 256);
+}
+
 template <int L>
 static void launch_mm(const CUtensorMap& ta, const CUtensorMap& tb, const tc::MmArgs& args,
                       unsigned grid, cudaStream_t st) {

@@ -11,6 +11,7 @@ namespace ccm {
 // 16 bits and the inner size keeps every digit-class sum below 2^24.
 bool matmul_tc_supported(const ccm_matrix& a, const ccm_matrix& b);
 size_t matmul_tc_workspace(const ccm_matrix& a, const ccm_matrix& b);
+size_t matmul_tc_workspace_upper(uint64_t m, uint64_t k, uint64_t n);
 // Writes the exact int64 product into `c_scratch` (m x n, row-major) and
 // merges its width statistics into c's header.
 int run_matmul_tc(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c,

@@ -119,8 +119,14 @@ void run_measure(const void* dense, int dtype, uint64_t rows, uint64_t cols, ccm
   note_launch();
 }
 
+size_t pack_workspace(uint64_t rows, uint64_t cols, uint64_t capacity) {
+  const uint64_t n = rows * cols;
+  const int cls = ew_class(width_bound(capacity, n));
+  return (cls && n) ? ge::pack_ws_bytes(n, cls) : 0;
+}
+
 void run_pack(const void* dense, int dtype, uint64_t rows, uint64_t cols, const ccm_matrix& out,
-              cudaStream_t st) {
+              void* ws, size_t ws_bytes, cudaStream_t st) {
   InitArgs ia{};
   ia.out = out.hdr;
   ia.out_rows = rows;
@@ -128,6 +134,24 @@ void run_pack(const void* dense, int dtype, uint64_t rows, uint64_t cols, const 
   launch_init(ia, st);
   uint64_t n = rows * cols;
   const int cls = ew_class(width_bound(out.capacity, n));
+  if (cls && n && ws && ws_bytes >= ge::pack_ws_bytes(n, cls)) {
+    // single pass over the dense input: local-width tiles, then re-code
+    ge::EwCall c{};
+    c.kind = dtype == CCM_I64 ? ge::EwKind::LocalI64 : ge::EwKind::LocalI32;
+    c.dense = dense;
+    c.out = out.hdr;
+    c.words = out.words;
+    c.capacity = out.capacity;
+    c.rows = rows;
+    c.cols = cols;
+    c.ws = ws;
+    profile_begin(st);
+    launch_ew(cls, c, st);
+    profile_end(st);
+    c.kind = ge::EwKind::Repack;
+    launch_ew(cls, c, st);
+    return;
+  }
   if (cls && n) {
     if (dtype == CCM_I64)
       launch_stats(ProdDenseI64{(const int64_t*)dense}, out.hdr, n, st);

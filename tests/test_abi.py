@@ -64,9 +64,11 @@ def test_host_side_rejections_launch_nothing(L):
     small = _m(30, 40, cap=4)
     assert L.ccm_scale(bp(_m(30, 40)), 2, bp(small), None) == ccm.E_CAPACITY
     # pack: bad dtype, NULL dense, shape disagreement
-    assert L.ccm_pack(ctypes.c_void_p(0x3000), 7, 3, 4, bp(c), None) == ccm.E_INVAL
-    assert L.ccm_pack(None, ccm.I64, 3, 4, bp(c), None) == ccm.E_INVAL
-    assert L.ccm_pack(ctypes.c_void_p(0x3000), ccm.I64, 4, 4, bp(c), None) == ccm.E_SHAPE
+    assert L.ccm_pack(ctypes.c_void_p(0x3000), 7, 3, 4, bp(c), None, 0, None) == ccm.E_INVAL
+    assert L.ccm_pack(None, ccm.I64, 3, 4, bp(c), None, 0, None) == ccm.E_INVAL
+    assert L.ccm_pack(ctypes.c_void_p(0x3000), ccm.I64, 4, 4, bp(c), None, 0, None) == ccm.E_SHAPE
+    assert L.ccm_pack(ctypes.c_void_p(0x3000), ccm.I64, 3, 4, bp(c), ctypes.c_void_p(0x10010),
+                      1 << 20, None) == ccm.E_INVAL
     # matvec: x shape, workspace size and alignment
     x, y = _m(4, 1), _m(3, 1)
     ws = ctypes.c_void_p(0x10000)

@@ -1,0 +1,111 @@
+"""Batched matvec (one persistent launch over many packed matrices of uneven
+shapes and widths) against the oracle and against one call per matrix."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import assert_same_packed, device, lib_ccm, to_dev, torch, words_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ccm():
+    device()
+    return lib_ccm()
+
+
+def _batch_inputs(seed, count, lo=1, hi=300, wlo=1, whi=24):
+    rows, cols, widths = synth.batch_shapes(seed, count, lo, hi, wlo, whi)
+    mats, xs = [], []
+    for i in range(count):
+        s = synth.batch_matrix_seed(seed, i)
+        b = int(widths[i])
+        a = synth.uniform_signed(s, synth.STREAM_A, int(rows[i] * cols[i]), b)
+        if i % 3 == 0:
+            a = np.abs(a)  # unsigned fields too
+        x = synth.uniform_signed(s, synth.STREAM_X, int(cols[i]), 8)
+        mats.append(a.reshape(int(rows[i]), int(cols[i])))
+        xs.append(x.reshape(-1, 1))
+    return mats, xs
+
+
+def _pack_exact(ccm, arr):
+    return ccm.pack(to_dev(arr))
+
+
+def test_batch_matches_oracle(ccm):
+    from paper_1303_0270_gb300.batch import BatchMatvec
+    mats, xs = _batch_inputs(77, 160)
+    # degenerate shapes: short rows, a single field, rows of exactly 32 and 33 fields
+    extra = [(1, 1), (5, 16), (3, 31), (2, 32), (4, 33), (1, 2048), (300, 1)]
+    for k, (r, c) in enumerate(extra):
+        mats.append(synth.uniform_signed(900 + k, 0, r * c, 11).reshape(r, c))
+        xs.append(synth.uniform_signed(950 + k, 0, c, 8).reshape(-1, 1))
+    pa = [_pack_exact(ccm, a) for a in mats]
+    px = [_pack_exact(ccm, x) for x in xs]
+    bm = BatchMatvec(pa, px, unit_segments=64)
+    bm.launch()
+    torch.cuda.synchronize()
+    for i, (a, x) in enumerate(zip(mats, xs)):
+        o = oracle.matvec(oracle.pack(a), oracle.pack(x))
+        assert_same_packed(bm.ys[i], o, f"batch entry {i} {a.shape}")
+
+
+def test_batch_equals_single_calls_and_graph_replay(ccm):
+    from paper_1303_0270_gb300.batch import BatchMatvec
+    mats, xs = _batch_inputs(78, 120, lo=16, hi=700)
+    pa = [_pack_exact(ccm, a) for a in mats]
+    px = [_pack_exact(ccm, x) for x in xs]
+    singles = [ccm.matvec(a, x) for a, x in zip(pa, px)]
+    bm = BatchMatvec(pa, px, unit_segments=256)
+    bm.run()  # captured graph
+    torch.cuda.synchronize()
+    for i in range(len(mats)):
+        assert np.array_equal(words_np(bm.ys[i]), words_np(singles[i]))
+        assert bm.ys[i].header().width == singles[i].header().width
+    # replay twice more: same words (the scratch is re-initialised every run)
+    first = [words_np(y).copy() for y in bm.ys]
+    bm.run()
+    bm.run()
+    torch.cuda.synchronize()
+    for i in range(len(mats)):
+        assert np.array_equal(words_np(bm.ys[i]), first[i])
+
+
+def test_batch_autotune_keeps_results(ccm, tmp_path):
+    from paper_1303_0270_gb300.batch import BatchMatvec
+    mats, xs = _batch_inputs(79, 60, lo=16, hi=500)
+    pa = [_pack_exact(ccm, a) for a in mats]
+    px = [_pack_exact(ccm, x) for x in xs]
+    bm = BatchMatvec(pa, px)
+    best = bm.autotune(candidates=[(64, 152), (256, 304), (1024, 608)], reps=2,
+                       cache=str(tmp_path / "tune.json"))
+    assert best["unit_segments"] in (64, 256, 1024)
+    bm.launch()
+    torch.cuda.synchronize()
+    for i, (a, x) in enumerate(zip(mats, xs)):
+        assert_same_packed(bm.ys[i], oracle.matvec(oracle.pack(a), oracle.pack(x)), f"tuned {i}")
+    # a second tuner on the same batch reads the cache
+    bm2 = BatchMatvec(pa, px)
+    again = bm2.autotune(cache=str(tmp_path / "tune.json"))
+    assert again["unit_segments"] == best["unit_segments"]
+
+
+def test_batch_errors(ccm):
+    from paper_1303_0270_gb300.batch import BatchMatvec
+    a = _pack_exact(ccm, synth.uniform_signed(1, 0, 12, 5).reshape(3, 4))
+    x_wrong = _pack_exact(ccm, synth.uniform_signed(2, 0, 5, 5).reshape(5, 1))
+    with pytest.raises(ccm.CCMError) as ei:
+        BatchMatvec([a], [x_wrong])
+    assert ei.value.status == ccm.E_SHAPE
+    # a 41-bit A is outside the kernel's widths: that entry alone reports it
+    wide = _pack_exact(ccm, np.full((3, 4), 1 << 40, dtype=np.int64))
+    x = _pack_exact(ccm, np.ones((4, 1), dtype=np.int64))
+    bm = BatchMatvec([wide, a], [x, x], ys=None)
+    bm.launch()
+    torch.cuda.synchronize()
+    assert bm.ys[0].status == ccm.E_WIDTH
+    assert np.array_equal(ccm.unpack(bm.ys[1].check()).cpu().numpy().ravel(),
+                          ccm.unpack(a).cpu().numpy() @ np.ones(4, dtype=np.int64))

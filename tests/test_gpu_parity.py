@@ -260,6 +260,9 @@ def test_width_class_and_runtime_kernels_agree(ccm, b):
     pa_fast, pa_rt = _pack_cap(ccm, a, b), _pack_cap(ccm, a, 64)
     pc_fast = _pack_cap(ccm, c, max(1, b - 1))
     assert_same_packed(pa_fast, oa, f"class pack b={b}")
+    two_pass = ccm.pack_into(to_dev(a), ccm.PackedMatrix(*shape, ccm.words_for(*shape, b), device()),
+                             single_pass=False)
+    assert_same_packed(two_pass, oa, f"two-pass class pack b={b}")
     assert_same_packed(pa_rt, oa, f"runtime pack b={b}")
     assert np.array_equal(ccm.unpack(pa_fast).cpu().numpy(), a)
     assert np.array_equal(ccm.unpack(pa_fast, dtype=torch.int32).cpu().numpy(), a)
