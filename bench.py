@@ -429,6 +429,75 @@ def run_batch(args, rank, world, local_rank):
     }
 
 
+def run_matmul_bench(args, rank, world, local_rank):
+    """Packed matmul: A, B 4096 x 4096 uniform over the signed b-bit range,
+    b in {4, 8, 12, 16}; exact int64 C re-packed at its width.  Tensor-core
+    digit path (tcgen05, e4m3 digits, fp32 accumulators) against the CUDA-core
+    decode-and-multiply path on the same inputs (results compared word for
+    word).  Useful ops = 2 * 4096^3 per matmul."""
+    import torch
+
+    import synth
+    from paper_1303_0270_gb300 import ccm
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    n = args.matmul_n
+    peaks_d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    fp8_peak = 2.0 * float(peaks_d["bf16_tflops"])  # measured bf16 x nominal fp8/bf16 ratio (2)
+    dense = torch.empty(n * n, dtype=torch.int64, device=dev)
+    results = []
+    for b in (4, 8, 12, 16):
+        lo, hi = synth.signed_range(b)
+        seed = SEED_A + 1000 * rank + b
+        ccm.gen_uniform(n * n, seed, synth.STREAM_A, lo, hi, out=dense)
+        pa = ccm.pack_into(dense.view(n, n), ccm.PackedMatrix(n, n, ccm.words_for(n, n, b), dev))
+        ccm.gen_uniform(n * n, seed, synth.STREAM_B, lo, hi, out=dense)
+        pb = ccm.pack_into(dense.view(n, n), ccm.PackedMatrix(n, n, ccm.words_for(n, n, b), dev))
+        cap = ccm.words_for(n, n, min(64, 2 * b + 14))
+        ws = ccm.workspace(ccm.OP_MATMUL, n, n, n, dev)
+        ct = ccm.PackedMatrix(n, n, cap, dev)
+        cc = ccm.PackedMatrix(n, n, cap, dev)
+        timings = {}
+        for name, path, out, reps in (("tensor", ccm.MATMUL_TENSOR, ct, args.steps),
+                                      ("cudacore", ccm.MATMUL_CUDACORE, cc, 2)):
+            for _ in range(2):
+                ccm.matmul_into(pa, pb, out, path=path, ws=ws)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            k0.record()
+            k1.record()
+            tot, kern = 0.0, 0.0
+            for _ in range(reps):
+                ccm.profile_next(k0, k1)
+                e0.record()
+                ccm.matmul_into(pa, pb, out, path=path, ws=ws)
+                e1.record()
+                e1.synchronize()
+                tot += e0.elapsed_time(e1)
+                kern += k0.elapsed_time(k1)
+            timings[name] = (tot / reps, kern / reps)
+        same = (ct.check().width == cc.check().width and torch.equal(ct.words(), cc.words()))
+        L = (b + 3) // 4
+        useful = 2.0 * n ** 3
+        t_all, t_mma = timings["tensor"]
+        results.append({
+            "b": b, "digits": L, "width_C": ct.width, "tensor_vs_cudacore_identical": bool(same),
+            "tensor_ms": round(t_all, 4), "tensor_mma_kernel_ms": round(t_mma, 4),
+            "useful_int_TOPS": round(useful / (t_all * 1e-3) / 1e12, 2),
+            "mma_kernel_fp8_TFLOPS": round(L * L * useful / (t_mma * 1e-3) / 1e12, 1),
+            "mma_frac_of_fp8_peak": round(L * L * useful / (t_mma * 1e-3) / 1e12 / fp8_peak, 4),
+            "cudacore_ms": round(timings["cudacore"][0], 3),
+            "cudacore_useful_int_TOPS": round(useful / (timings["cudacore"][0] * 1e-3) / 1e12, 3),
+            "speedup_tensor_vs_cudacore": round(timings["cudacore"][0] / t_all, 2),
+        })
+    return {"metric": METRIC, "workload": "packed matmul", "unit": "int-TOPS (useful)",
+            "value": round(statistics.mean(r["useful_int_TOPS"] for r in results), 2),
+            "n": n, "fp8_peak_TFLOPS": fp8_peak,
+            "fp8_peak_source": "MEASURED_PEAKS bf16_tflops x 2 (nominal fp8/bf16 ratio)",
+            "results": results}
+
+
 def run_e2e(wl, torch, args, barrier, dist, dev, world, step_bytes):
     """Same step through the public API with host buffers: pinned host -> device
     copies of the dense inputs, the step, and device -> host copies of every
@@ -547,7 +616,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ccm", choices=["ccm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="step", choices=["step", "batch"])
+    ap.add_argument("--workload", default="step", choices=["step", "batch", "matmul"])
+    ap.add_argument("--matmul-n", type=int, default=4096)
     ap.add_argument("--batch-count", type=int, default=10000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -567,8 +637,9 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    if args.workload == "batch":
-        line = run_batch(args, rank, world, local_rank)
+    if args.workload in ("batch", "matmul"):
+        fn = run_batch if args.workload == "batch" else run_matmul_bench
+        line = fn(args, rank, world, local_rank)
         if rank == 0:
             print(json.dumps(line), flush=True)
         return
