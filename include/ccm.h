@@ -254,6 +254,30 @@ ccm_status ccm_batch_plan(const ccm_batch_entry* entries, int count, uint32_t un
 ccm_status ccm_batch_matvec(const void* plan, const ccm_batch_info* info, void* ws,
                             size_t ws_bytes, int grid, ccm_stream_t stream);
 
+/* Matvec that allocates nothing (the paper has no counterpart; this is a
+ * service of the library).  For callers that cannot hand ccm_matvec a device
+ * workspace because they must not allocate device memory: a process whose
+ * GPU memory is reserved in full by another component's allocator, or a
+ * latency-critical path that cannot afford the device-wide synchronisation a
+ * cudaMalloc/cudaFree may cause.  Same operation, arguments and results as
+ * ccm_matvec, minus the workspace: the scratch is a fixed array of
+ * CCM_STATIC_SCRATCH_BYTES compiled into libccm, present on every GPU that
+ * loads the library until the process exits.
+ *  - Size limit: the matvec scratch for A (rows x cols) is 8*cols + 8*rows
+ *    bytes plus alignment; larger problems return CCM_E_CAPACITY at once
+ *    (rows + cols up to about 131,000).
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture.
+ *  - All calls on a device share the one array and find in it whatever the
+ *    previous call left; the kernels clear what must start at zero.  Calls
+ *    that overlap on the GPU (for example on two unordered streams) race on
+ *    the array: order them.
+ *  - No cudaMalloc, cudaFree or other allocating call is made. */
+#define CCM_STATIC_SCRATCH_BYTES ((1u << 20) + 4096u)
+ccm_status ccm_matvec_static(const ccm_matrix* a, const ccm_matrix* x, const ccm_matrix* y,
+                             ccm_stream_t stream);
+
 /* Runtime instrumentation (no counterpart in the paper).
  * ccm_launch_count: number of kernels this library has launched in this
  * process so far (all devices, all threads).

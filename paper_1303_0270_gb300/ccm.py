@@ -83,6 +83,7 @@ SIGNATURES = {
     "ccm_batch_plan": ([ctypes.POINTER(BatchEntry), _i32, ctypes.c_uint32, _vp, _sz,
                         ctypes.POINTER(BatchInfo)], _i32),
     "ccm_batch_matvec": ([_vp, ctypes.POINTER(BatchInfo), _vp, _sz, _i32, _vp], _i32),
+    "ccm_matvec_static": ([_MP, _MP, _MP, _vp], _i32),
     "ccm_launch_count": ([], _u64),
     "ccm_profile_next": ([_vp, _vp], _i32),
 }
