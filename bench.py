@@ -498,6 +498,64 @@ def run_matmul_bench(args, rank, world, local_rank):
             "results": results}
 
 
+def run_serve_bench(args, rank, world, local_rank):
+    """Serving: a store of packed matrices (dims log-uniform in [64, 8192),
+    widths U{2..20}) resident on the GPU, a Poisson stream of requests (60 %
+    matvec on a store matrix, 30 % pack of a new dense matrix, 10 % matmul of
+    two store matrices with dims <= 2048), admitted by memory and continuously
+    batched.  Saturation throughput first (everything arrives at t = 0), then
+    p50/p99 at 50 % and 80 % of it, against one launch sequence per request on
+    one stream for the same 80 % trace."""
+    import torch
+
+    from paper_1303_0270_gb300 import serve
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    t0 = time.perf_counter()
+    store, store_bytes = serve.build_store(SEED_A + rank, int(args.store_gb * (1 << 30)), 64, 8192,
+                                           2, 20, dev)
+    t_store = time.perf_counter() - t0
+    budget = store_bytes + int(args.serve_budget_gb * (1 << 30))
+    n = args.serve_requests
+
+    def run(rate, batching=True, streams=4, seed=SEED_B):
+        trace = serve.build_trace(seed, store, n, rate, dev)
+        srv = serve.Server(store, mem_budget=budget, streams=streams, batching=batching)
+        torch.cuda.synchronize(dev)
+        w0 = time.perf_counter()
+        st = srv.run(trace)
+        wall = time.perf_counter() - w0
+        return st.summary(wall), trace
+
+    run(float("inf"))  # warm-up (autotune-free, builds plans, first launches)
+    sat, _ = run(float("inf"))
+    rate_sat = sat["throughput_rps"]
+    at50, _ = run(0.5 * rate_sat)
+    at80, trace80 = run(0.8 * rate_sat)
+    plain80, _ = run(0.8 * rate_sat, batching=False, streams=1)
+    plain_sat, _ = run(float("inf"), batching=False, streams=1)
+    # results: the same alone and in the mix (sample of the 80 % trace)
+    bad = 0
+    for r in trace80[:: max(1, len(trace80) // 64)]:
+        alone = serve.run_alone(store, r, dev)
+        if not (torch.equal(r.out.words(), alone.words()) and
+                r.out.header().width == alone.header().width):
+            bad += 1
+    return {
+        "metric": METRIC, "workload": "serving", "unit": "requests/s",
+        "value": at80["throughput_rps"], "n_gpus": world, "data": "synthetic",
+        "config": {"store_bytes": store_bytes, "store_matrices": len(store),
+                   "store_build_s": round(t_store, 1), "requests": n,
+                   "mix": "60% matvec / 30% pack / 10% matmul", "mem_budget": budget,
+                   "streams": 4},
+        "saturation": sat, "at_50pct": at50, "at_80pct": at80,
+        "plain_one_launch_per_request_at_80pct": plain80,
+        "plain_saturation": plain_sat,
+        "speedup_saturation_vs_plain": round(rate_sat / plain_sat["throughput_rps"], 2),
+        "mismatches_alone_vs_mix": bad,
+    }
+
+
 def run_e2e(wl, torch, args, barrier, dist, dev, world, step_bytes):
     """Same step through the public API with host buffers: pinned host -> device
     copies of the dense inputs, the step, and device -> host copies of every
@@ -616,7 +674,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ccm", choices=["ccm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="step", choices=["step", "batch", "matmul"])
+    ap.add_argument("--workload", default="step", choices=["step", "batch", "matmul", "serve"])
+    ap.add_argument("--store-gb", type=float, default=8.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=16.0)
+    ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--matmul-n", type=int, default=4096)
     ap.add_argument("--batch-count", type=int, default=10000)
     args = ap.parse_args()
@@ -637,8 +698,8 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    if args.workload in ("batch", "matmul"):
-        fn = run_batch if args.workload == "batch" else run_matmul_bench
+    if args.workload in ("batch", "matmul", "serve"):
+        fn = {"batch": run_batch, "matmul": run_matmul_bench, "serve": run_serve_bench}[args.workload]
         line = fn(args, rank, world, local_rank)
         if rank == 0:
             print(json.dumps(line), flush=True)

@@ -213,7 +213,7 @@ ccm_status ccm_gen_poisson(int64_t* out, uint64_t count, uint64_t seed, uint64_t
 /* ---------------------------------------------------------------------------
  * Batched matvec: y_i = A_i x_i for many packed matrices of uneven shapes and
  * widths in one persistent launch (same arithmetic as ccm_matvec, applied to
- * every entry).  Limits per entry: cols <= 2048 (checked on the host);
+ * every entry).  Limits per entry: cols <= 8192 (checked on the host);
  * width(A) <= 32, width(x) <= 31 and width(A) + width(x) + bitlen(cols) <= 63
  * so that every sum fits int64 (checked on the GPU: an entry outside them gets
  * CCM_E_WIDTH in its y header and the other entries are unaffected).
@@ -228,7 +228,7 @@ ccm_status ccm_gen_poisson(int64_t* out, uint64_t count, uint64_t seed, uint64_t
  *
  * ccm_batch_matvec launches an initialisation kernel (validates the headers,
  * clears y headers and the scratch) and the persistent kernel (`grid` CTAs;
- * <= 0 picks 4 per SM).  `ws` is device workspace of at least
+ * <= 0 picks 3 per SM).  `ws` is device workspace of at least
  * ccm_batch_workspace_bytes(...) bytes, 256-byte aligned.  Each y_i header
  * receives its own status.  Both launches are stream-ordered and can be
  * captured in a CUDA graph. */

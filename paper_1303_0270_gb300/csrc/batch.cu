@@ -30,7 +30,7 @@ namespace bt {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kMaxCols = 2048;      // x of at most 2048 entries per matrix
+constexpr int kMaxCols = 8192;      // x of at most 8192 entries per matrix (32 KB of shared)
 constexpr int kWordsPerWarp = 32 * 32 + 64;  // staging for 32 segments of width <= 32
 
 struct Mat {
@@ -227,7 +227,7 @@ __device__ void pack_y(const Mat& M, const int64_t* __restrict__ ys, uint64_t* s
 }
 
 __global__ void __launch_bounds__(kThreads) k_batch_mv(Args a) {
-  __shared__ __align__(16) int4 s_x4[kMaxCols / 4];
+  extern __shared__ __align__(16) int4 s_x4[];  // kMaxCols ints
   __shared__ uint32_t s_stage[kWarps][kWordsPerWarp];
   __shared__ uint32_t s_unit;
   __shared__ int s_last;
@@ -426,9 +426,15 @@ ccm_status ccm_batch_matvec(const void* plan, const ccm_batch_info* info, void* 
   const uint64_t init_items = ccm::umax(info->y_rows, info->count);
   int gi = (int)ccm::umin((init_items + 255) / 256, (uint64_t)ccm::num_sms() * 8);
   k_batch_init<<<gi < 1 ? 1 : gi, 256, 0, st>>>(a, info->y_rows);
-  if (grid <= 0) grid = ccm::num_sms() * 4;
+  if (grid <= 0) grid = ccm::num_sms() * 3;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_batch_mv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kMaxCols * (int)sizeof(int));
+    attr = true;
+  }
   ccm::profile_begin(st);
-  k_batch_mv<<<grid, kThreads, 0, st>>>(a);
+  k_batch_mv<<<grid, kThreads, kMaxCols * sizeof(int), st>>>(a);
   ccm::profile_end(st);
   ccm::note_launch(2);
   return cudaGetLastError() == cudaSuccess ? CCM_OK : CCM_E_CUDA;
