@@ -243,7 +243,7 @@ typedef struct ccm_batch_info {
   uint32_t units;         /* work units */
   uint64_t y_rows;        /* sum of the entries' rows */
   uint32_t unit_segments; /* segments per unit */
-  uint32_t reserved;
+  uint32_t max_cols;      /* widest entry (sizes the kernel's shared memory) */
   uint64_t plan_bytes;
 } ccm_batch_info;
 

@@ -393,7 +393,10 @@ ccm_status ccm_batch_plan(const ccm_batch_entry* entries, int count, uint32_t un
       units[u].nseg = (uint32_t)(s ? ccm::umin(unit_segments, s - k * unit_segments) : 0);
     }
   }
+  uint64_t maxcols = 0;
+  for (int i = 0; i < count; ++i) maxcols = ccm::umax(maxcols, entries[i].a.cols);
   info->count = (uint32_t)count;
+  info->max_cols = (uint32_t)maxcols;
   info->units = L.nunits;
   info->y_rows = L.yrows;
   info->unit_segments = unit_segments;
@@ -426,15 +429,17 @@ ccm_status ccm_batch_matvec(const void* plan, const ccm_batch_info* info, void* 
   const uint64_t init_items = ccm::umax(info->y_rows, info->count);
   int gi = (int)ccm::umin((init_items + 255) / 256, (uint64_t)ccm::num_sms() * 8);
   k_batch_init<<<gi < 1 ? 1 : gi, 256, 0, st>>>(a, info->y_rows);
+  // x of the widest entry in shared memory (rounded to whole 32-field segments)
+  const size_t xbytes = (size_t)((info->max_cols + 31) / 32 * 32) * sizeof(int) + 16;
   if (grid <= 0) grid = ccm::num_sms() * 3;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_batch_mv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kMaxCols * (int)sizeof(int));
+                         kMaxCols * (int)sizeof(int) + 16);
     attr = true;
   }
   ccm::profile_begin(st);
-  k_batch_mv<<<grid, kThreads, kMaxCols * sizeof(int), st>>>(a);
+  k_batch_mv<<<grid, kThreads, xbytes, st>>>(a);
   ccm::profile_end(st);
   ccm::note_launch(2);
   return cudaGetLastError() == cudaSuccess ? CCM_OK : CCM_E_CUDA;

@@ -96,6 +96,73 @@ __global__ void __launch_bounds__(kMmThreads) k_matmul_cc(ccm_header* out, const
   }
 }
 
+// CUDA-core path for fields of at most 31 bits (bounded by the capacities):
+// 128 x 128 output tiles, 256 threads with 8 x 8 outputs each; A and B tiles
+// decoded to int32 in shared memory; every product a 32 x 32 -> 64-bit
+// multiply-add.  The host selects it only when b_a + b_b + bitlen(k) <= 63,
+// so every partial sum fits the int64 accumulators.
+constexpr int kCB = 128, kCK = 16;
+__global__ void __launch_bounds__(256) k_matmul_cc32(ccm_header* out, const ccm_header* ha,
+                                                     const uint32_t* __restrict__ wa,
+                                                     const ccm_header* hb,
+                                                     const uint32_t* __restrict__ wb,
+                                                     uint64_t m, uint64_t k, uint64_t n,
+                                                     int64_t* __restrict__ c) {
+  __shared__ __align__(16) int sA[kCK][kCB + 4];
+  __shared__ __align__(16) int sB[kCK][kCB + 4];
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = out->status != CCM_OK;
+  __syncthreads();
+  if (s_skip) return;
+  const int ba = ha->width, sa = ha->is_signed, bb = hb->width, sb = hb->is_signed;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const uint64_t tiles_n = (n + kCB - 1) / kCB;
+  const uint64_t tiles = ((m + kCB - 1) / kCB) * tiles_n;
+  for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const uint64_t tm = (t / tiles_n) * kCB, tn = (t % tiles_n) * kCB;
+    long long acc[8][8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[r][q] = 0;
+    for (uint64_t k0 = 0; k0 < k; k0 += kCK) {
+      for (int e = threadIdx.x; e < kCB * kCK; e += 256) {
+        const int r = e / kCK, kk = e % kCK;
+        const uint64_t gi = tm + r, gk = k0 + kk;
+        sA[kk][r] = (gi < m && gk < k) ? (int)decode_field(wa, gi * k + gk, ba, sa) : 0;
+        const int kk2 = e / kCB, q = e % kCB;
+        const uint64_t gk2 = k0 + kk2, gj = tn + q;
+        sB[kk2][q] = (gk2 < k && gj < n) ? (int)decode_field(wb, gk2 * n + gj, bb, sb) : 0;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < kCK; ++kk) {
+        const int4 a0 = *reinterpret_cast<const int4*>(&sA[kk][ty * 4]);
+        const int4 a1 = *reinterpret_cast<const int4*>(&sA[kk][64 + ty * 4]);
+        const int4 b0 = *reinterpret_cast<const int4*>(&sB[kk][tx * 4]);
+        const int4 b1 = *reinterpret_cast<const int4*>(&sB[kk][64 + tx * 4]);
+        const int av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const int bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) acc[r][q] += (long long)av[r] * bv[q];
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const uint64_t gi = tm + (r < 4 ? ty * 4 + r : 64 + ty * 4 + r - 4);
+      if (gi >= m) continue;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const uint64_t gj = tn + (q < 4 ? tx * 4 + q : 64 + tx * 4 + q - 4);
+        if (gj < n) c[gi * n + gj] = acc[r][q];
+      }
+    }
+  }
+}
+
 }  // namespace
 
 size_t matmul_workspace(const ccm_matrix& a, const ccm_matrix& b) {
@@ -141,10 +208,17 @@ int run_matmul(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, in
       run_pack_scratch(cs, c, st, /*stats_done=*/true);
       return CCM_OK;
     } else {
-      uint64_t tiles = ((m + kBM - 1) / kBM) * ((n + kBN - 1) / kBN);
-      int g = (int)umin(tiles, (uint64_t)num_sms() * 4);
+      const int ba = width_bound(a.capacity, m * k), bb = width_bound(b.capacity, k * n);
       profile_begin(st);
-      k_matmul_cc<<<g, kMmThreads, 0, st>>>(c.hdr, a.hdr, a.words, b.hdr, b.words, m, k, n, cs);
+      if (ba <= 31 && bb <= 31 && ba + bb + bitlen_host(k) <= 63) {
+        uint64_t tiles = ((m + kCB - 1) / kCB) * ((n + kCB - 1) / kCB);
+        int g = (int)umin(tiles, (uint64_t)num_sms() * 2);
+        k_matmul_cc32<<<g, 256, 0, st>>>(c.hdr, a.hdr, a.words, b.hdr, b.words, m, k, n, cs);
+      } else {
+        uint64_t tiles = ((m + kBM - 1) / kBM) * ((n + kBN - 1) / kBN);
+        int g = (int)umin(tiles, (uint64_t)num_sms() * 4);
+        k_matmul_cc<<<g, kMmThreads, 0, st>>>(c.hdr, a.hdr, a.words, b.hdr, b.words, m, k, n, cs);
+      }
       profile_end(st);
       note_launch();
     }

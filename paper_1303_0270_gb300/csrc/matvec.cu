@@ -90,6 +90,16 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec_rows(ccm_header* out, con
 
 }  // namespace
 
+namespace mvf {
+int resident_ctas_8(int threads, size_t smem);
+int resident_ctas_16(int threads, size_t smem);
+int resident_ctas_32(int threads, size_t smem);
+int resident_ctas(int bmax, int threads, size_t smem) {
+  return bmax <= 8 ? resident_ctas_8(threads, smem)
+                   : bmax <= 16 ? resident_ctas_16(threads, smem) : resident_ctas_32(threads, smem);
+}
+}  // namespace mvf
+
 size_t matvec_workspace(uint64_t m, uint64_t n) {
   auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
   return up(n * sizeof(int64_t)) + up(m * sizeof(int64_t)) + 256;
@@ -126,16 +136,26 @@ void run_matvec(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& y, v
     const int warps = bmax_a <= 12 ? 8 : 4;
     const uint64_t row_blocks = (m + 32 * warps - 1) / (32 * warps);
     const uint64_t groups = n / mvf::kKC;  // 128-column groups
-    const uint64_t target = (uint64_t)num_sms() * 8;
-    uint64_t splits = umin(umax((target + row_blocks - 1) / row_blocks, 1), groups);
+    const size_t stage_region = (size_t)warps * mvf::kStages * 32 * mvf::pitch_bytes(bmax_a);
+    // one wave: as many CTAs as stay resident; column slabs split the work
+    // when there are fewer row blocks than that, CTAs loop over row blocks
+    // when there are more
+    const int per_sm0 = mvf::resident_ctas(bmax_a, warps * 32,
+                                           stage_region + umin(n, 1024) * sizeof(int));
+    const uint64_t resident0 = (uint64_t)num_sms() * (uint64_t)(per_sm0 > 0 ? per_sm0 : 1);
+    uint64_t splits = umin(umax(resident0 / umax(row_blocks, 1), 1), groups);
     splits = umin(splits, 65535);
     const uint64_t per = (groups + splits - 1) / splits;
     splits = (groups + per - 1) / per;
+    const int per_sm = mvf::resident_ctas(bmax_a, warps * 32,
+                                          stage_region + per * mvf::kKC * sizeof(int));
+    const uint64_t resident = (uint64_t)num_sms() * (uint64_t)(per_sm > 0 ? per_sm : 1);
+    const uint64_t grid_x = umin(row_blocks, umax(resident / splits, 1));
     mvf::Args args{y.hdr, a.hdr, a.words, x.hdr, x.words, m, n,
                    (uint32_t)(per * mvf::kKC), 0u, yv};
-    args.stage_region = (uint32_t)(warps * mvf::kStages * 32 * mvf::pitch_bytes(bmax_a));
+    args.stage_region = (uint32_t)stage_region;
     const size_t smem = args.stage_region + per * mvf::kKC * sizeof(int);
-    dim3 grid((unsigned)row_blocks, (unsigned)splits);
+    dim3 grid((unsigned)grid_x, (unsigned)splits);
     profile_begin(st);
     const bool narrow = bmax_a + bmax_x + 7 <= 31;
     if (bmax_a <= 8)

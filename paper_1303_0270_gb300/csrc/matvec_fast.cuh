@@ -129,29 +129,40 @@ __device__ __noinline__ void body(const Args& a, uint8_t* smem, int* xs, uint64_
   const int pitch = pitch_bytes(B);
   const int stage_bytes = 32 * pitch;
   uint8_t* wbuf = smem + warp * kStages * stage_bytes;
-  const uint64_t row0 = (uint64_t)blockIdx.x * blockDim.x + (uint64_t)warp * 32;
   const uint32_t nst = ncols / kKC;
-  long long acc = 0;
-  if (row0 < a.m) {
-    issue_stage<B>(a, wbuf, row0, col0, lane);
-    cp_async_commit();
-  }
-  __syncthreads();  // x slab decoded by the whole CTA
-  if (row0 < a.m) {
-    for (uint32_t s = 0; s < nst; ++s) {
-      if (s + 1 < nst) issue_stage<B>(a, wbuf + ((s + 1) % kStages) * stage_bytes, row0,
-                                      col0 + (uint64_t)(s + 1) * kKC, lane);
+  const uint64_t rows_per_cta = (uint64_t)blockDim.x;  // 32 rows per warp
+  const uint64_t nrb = (a.m + rows_per_cta - 1) / rows_per_cta;
+  bool first = true;
+  // persistent over row blocks: the CTA keeps its column slab (and x)
+  for (uint64_t rb = blockIdx.x; rb < nrb; rb += gridDim.x) {
+    const uint64_t row0 = rb * rows_per_cta + (uint64_t)warp * 32;
+    long long acc = 0;
+    if (row0 < a.m) {
+      issue_stage<B>(a, wbuf, row0, col0, lane);
       cp_async_commit();
-      cp_async_wait<1>();
-      __syncwarp();
-      decode_mac<B, SGN, NARROW>(wbuf + (s % kStages) * stage_bytes + lane * pitch, xs + s * kKC,
-                                 acc);
-      __syncwarp();
     }
-    if (row0 + lane < a.m)
-      atomicAdd(reinterpret_cast<unsigned long long*>(a.y + row0 + lane), (unsigned long long)acc);
+    if (first) {
+      __syncthreads();  // x slab decoded by the whole CTA
+      first = false;
+    }
+    if (row0 < a.m) {
+      for (uint32_t s = 0; s < nst; ++s) {
+        if (s + 1 < nst) issue_stage<B>(a, wbuf + ((s + 1) % kStages) * stage_bytes, row0,
+                                        col0 + (uint64_t)(s + 1) * kKC, lane);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncwarp();
+        decode_mac<B, SGN, NARROW>(wbuf + (s % kStages) * stage_bytes + lane * pitch, xs + s * kKC,
+                                   acc);
+        __syncwarp();
+      }
+      if (row0 + lane < a.m)
+        atomicAdd(reinterpret_cast<unsigned long long*>(a.y + row0 + lane), (unsigned long long)acc);
+    }
+    cp_async_wait<0>();
+    __syncwarp();
   }
-  cp_async_wait<0>();
+  if (first) __syncthreads();  // (a CTA with no row block still meets the barrier)
 }
 
 // Calls body<b, sign> for the runtime width b, for widths up to BMAX.
@@ -191,6 +202,10 @@ __global__ void __launch_bounds__(256) k_matvec_fast(Args a) {
     xs[j] = (int)decode_field(a.wx, col0 + j, bx, sx);
   dispatch<BMAX, NARROW>(a, b, sgn, smem, xs, col0, ncols);
 }
+
+// CTAs of the class kernel for bmax that fit on one SM with `threads`
+// threads and `smem` bytes of dynamic shared memory (host).
+int resident_ctas(int bmax, int threads, size_t smem);
 
 // Host launchers, one translation unit per class (matvec_fast{8,16,32}.cu).
 // `narrow`: the width bounds give b_a + b_x + 7 <= 31, so 128 products add up

@@ -17,6 +17,16 @@ static void launch(const Args& a, dim3 grid, int threads, size_t smem, cudaStrea
   k_matvec_fast<16, NARROW><<<grid, threads, smem, st>>>(a);
 }
 
+int resident_ctas_16(int threads, size_t smem) {
+  int n = 0;
+  cudaFuncSetAttribute(k_matvec_fast<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       227 * 1024);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_matvec_fast<16, true>, threads, smem) !=
+      cudaSuccess)
+    return 1;
+  return n;
+}
+
 void launch_matvec_fast16(const Args& a, bool narrow, dim3 grid, int threads, size_t smem,
                          cudaStream_t st) {
   if (narrow)
