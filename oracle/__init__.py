@@ -73,6 +73,14 @@ def lib():
         L.ccmo_matvec_rows.restype = i32
         L.ccmo_matmul_rows.argtypes = [vp, vp, u64, u64, u64, vp, sz, vp]
         L.ccmo_matmul_rows.restype = i32
+        L.ccmo_vlb_prefix_width.argtypes = [vp, sz]
+        L.ccmo_vlb_prefix_width.restype = i32
+        L.ccmo_vlb_bits.argtypes = [vp, sz, i32]
+        L.ccmo_vlb_bits.restype = u64
+        L.ccmo_vlb_pack.argtypes = [vp, sz, i32, vp, sz]
+        L.ccmo_vlb_pack.restype = u64
+        L.ccmo_vlb_unpack.argtypes = [vp, sz, i32, vp]
+        L.ccmo_vlb_unpack.restype = None
         _lib = L
     return _lib
 
@@ -233,3 +241,31 @@ def matvec(pa: Packed, px: Packed) -> Packed:
 def matmul(pa: Packed, pb: Packed) -> Packed:
     assert pa.cols == pb.rows
     return pack(matmul_dense(unpack(pa), unpack(pb)))
+
+
+# VLB, Method 2: a k-bit length prefix then the entry in its own bit length.
+@dataclass
+class Vlb:
+    n: int
+    k: int
+    nbits: int
+    words: np.ndarray  # uint32, zero padded to a multiple of 4 words
+
+
+def vlb_pack(values) -> Vlb:
+    a = _i64(values).ravel()
+    k = lib().ccmo_vlb_prefix_width(_ptr(a), a.size)
+    if k < 0:
+        raise ValueError("VLB takes non-negative entries")
+    nbits = int(lib().ccmo_vlb_bits(_ptr(a), a.size, k))
+    nw = ((nbits + 31) // 32 + 3) // 4 * 4
+    words = np.zeros(nw, dtype=np.uint32)
+    used = int(lib().ccmo_vlb_pack(_ptr(a), a.size, k, _ptr(words), nw))
+    assert used == nbits
+    return Vlb(a.size, k, nbits, words)
+
+
+def vlb_unpack(v: Vlb) -> np.ndarray:
+    out = np.empty(v.n, dtype=np.int64)
+    lib().ccmo_vlb_unpack(_ptr(v.words), v.n, v.k, _ptr(out))
+    return out

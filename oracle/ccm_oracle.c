@@ -184,3 +184,65 @@ int ccmo_matmul_rows(const int64_t* a, const int64_t* b, uint64_t m, uint64_t k,
   free(work);
   return status;
 }
+
+/* ---------------------------------------------------------------------------
+ * VLB, Method 2 (Methods, "Method 2: Variable Length Blocks", Eq. 9-13):
+ * every entry is written as a fixed k-bit prefix holding its bit length L,
+ * followed by the entry itself in exactly L bits, both LSB-first into the
+ * same stream as SM uses.  k is the bit length of the largest bit length
+ * (1023 -> 10 -> k = 4).  The bit length of 0 is taken as 1 (Eq. 1).
+ * Non-negative entries only, as in the paper.
+ * ------------------------------------------------------------------------- */
+static int vlb_len(int64_t v) {
+  int len = ccmo_bitlen_u64((uint64_t)v);
+  return len ? len : 1;
+}
+
+/* k, or -1 when an entry is negative. */
+int ccmo_vlb_prefix_width(const int64_t* a, size_t n) {
+  int lmax = 1;
+  for (size_t e = 0; e < n; ++e) {
+    if (a[e] < 0) return -1;
+    int len = vlb_len(a[e]);
+    if (len > lmax) lmax = len;
+  }
+  return ccmo_bitlen_u64((uint64_t)lmax);
+}
+
+uint64_t ccmo_vlb_bits(const int64_t* a, size_t n, int k) {
+  uint64_t bits = 0;
+  for (size_t e = 0; e < n; ++e) bits += (uint64_t)k + (uint64_t)vlb_len(a[e]);
+  return bits;
+}
+
+static void put_bit(uint32_t* words, uint64_t pos, uint32_t bit) {
+  words[pos / 32] |= bit << (pos % 32);
+}
+
+static uint32_t get_bit(const uint32_t* words, uint64_t pos) {
+  return (words[pos / 32] >> (pos % 32)) & 1u;
+}
+
+/* Writes the stream one bit at a time; returns the number of bits. */
+uint64_t ccmo_vlb_pack(const int64_t* a, size_t n, int k, uint32_t* words, size_t nwords) {
+  memset(words, 0, nwords * sizeof(uint32_t));
+  uint64_t pos = 0;
+  for (size_t e = 0; e < n; ++e) {
+    int len = vlb_len(a[e]);
+    for (int i = 0; i < k; ++i) put_bit(words, pos++, (uint32_t)((len >> i) & 1));
+    for (int i = 0; i < len; ++i) put_bit(words, pos++, (uint32_t)(((uint64_t)a[e] >> i) & 1u));
+  }
+  return pos;
+}
+
+/* Reads n entries back in order (each prefix tells how long the entry is). */
+void ccmo_vlb_unpack(const uint32_t* words, size_t n, int k, int64_t* out) {
+  uint64_t pos = 0;
+  for (size_t e = 0; e < n; ++e) {
+    int len = 0;
+    for (int i = 0; i < k; ++i) len |= (int)get_bit(words, pos++) << i;
+    uint64_t v = 0;
+    for (int i = 0; i < len; ++i) v |= (uint64_t)get_bit(words, pos++) << i;
+    out[e] = (int64_t)v;
+  }
+}
