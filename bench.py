@@ -242,7 +242,7 @@ def kernel_traffic(kernel: str):
     import hashlib
     for line in open(path):
         p = line.split("#", 1)[0].split()
-        if len(p) >= 4 and p[0] == kernel:
+        if len(p) >= 4 and p[0] == kernel.replace(" ", ""):
             src_hash = hashlib.sha256()
             for f in p[3].split(","):
                 src_hash.update(open(os.path.join(ROOT, f), "rb").read())
