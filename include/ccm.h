@@ -107,7 +107,12 @@ typedef struct ccm_matrix {
 } ccm_matrix;
 
 /* Operation codes for ccm_workspace_bytes. */
-typedef enum ccm_op { CCM_OP_MATVEC = 1, CCM_OP_MATMUL = 2, CCM_OP_PACK = 3 } ccm_op;
+typedef enum ccm_op {
+  CCM_OP_MATVEC = 1,
+  CCM_OP_MATMUL = 2,
+  CCM_OP_PACK = 3,
+  CCM_OP_VLB = 4
+} ccm_op;
 
 /* Matmul paths. */
 typedef enum ccm_matmul_path {
@@ -165,13 +170,17 @@ ccm_status ccm_get(const ccm_matrix* a, const uint64_t* idx, uint64_t count, int
                    int32_t* err, ccm_stream_t stream);
 
 /* C = A + B, exact, entrywise; A, B and C have the same shape; A and B may
- * have different widths and sign modes.  C is re-packed at its own width. */
-ccm_status ccm_add(const ccm_matrix* a, const ccm_matrix* b, const ccm_matrix* c,
-                   ccm_stream_t stream);
+ * have different widths and sign modes.  C is re-packed at its own width.
+ * `ws` (optional, as for ccm_pack: ccm_workspace_bytes(CCM_OP_PACK, rows,
+ * cols, c->capacity) bytes) lets the inputs be decoded once instead of twice;
+ * NULL takes the two-pass route.  The result is the same either way. */
+ccm_status ccm_add(const ccm_matrix* a, const ccm_matrix* b, const ccm_matrix* c, void* ws,
+                   size_t ws_bytes, ccm_stream_t stream);
 
 /* C = s * A for an int64 scalar s, exact; CCM_E_OVERFLOW when an entry does
- * not fit int64.  C is re-packed at its own width. */
-ccm_status ccm_scale(const ccm_matrix* a, int64_t s, const ccm_matrix* c, ccm_stream_t stream);
+ * not fit int64.  C is re-packed at its own width.  `ws` as for ccm_add. */
+ccm_status ccm_scale(const ccm_matrix* a, int64_t s, const ccm_matrix* c, void* ws,
+                     size_t ws_bytes, ccm_stream_t stream);
 
 /* y = A x: A is m x n, x is a packed n x 1 matrix, y a packed m x 1 matrix,
  * y_i = sum_j a_ij x_j exactly (CCM_E_OVERFLOW when y_i does not fit int64).
@@ -253,6 +262,35 @@ ccm_status ccm_batch_plan(const ccm_batch_entry* entries, int count, uint32_t un
                           void* plan, size_t plan_bytes, ccm_batch_info* info);
 ccm_status ccm_batch_matvec(const void* plan, const ccm_batch_info* info, void* ws,
                             size_t ws_bytes, int grid, ccm_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * VLB, the paper's second encoding (Methods, "Method 2: Variable Length
+ * Blocks", Eq. 9-13): each entry is a k-bit prefix holding its bit length L
+ * (the bit length of 0 is 1, Eq. 1) followed by the entry in L bits, LSB-first
+ * in one stream of 32-bit words; k is the bit length of the largest L.
+ * Non-negative entries only (a negative entry: CCM_E_RANGE in the header).
+ * Header: magic CCM_VLB_MAGIC, width = k, nwords, rows, cols, stat_or = total
+ * bits of the stream, reserved0 = largest L.  Because entries have no fixed
+ * position, the encoder also writes an index: the bit offset of every
+ * CCM_VLB_INDEX_STRIDE-th entry, plus the total bits as the last entry
+ * (ccm_vlb_index_entries(rows, cols) uint64 values, device) -- the decoder
+ * needs it; the paper's format has no index.
+ * ccm_vlb_pack: `dense` as for ccm_pack; `words` NULL measures only (header
+ * gets k, total bits and nwords: the size to compare with SM's rows*cols*b
+ * bits, Eq. 15 vs Eq. 16).  `ws`: ccm_workspace_bytes(CCM_OP_VLB, rows,
+ * cols, 0) bytes, 256-byte aligned.  A stream needing more than `capacity`
+ * words: CCM_E_CAPACITY in the header.
+ * ccm_vlb_unpack: entries back to `dense` (`dtype`); CCM_I32 needs L <= 31.
+ * Status to `*err` (device, may be NULL) as for ccm_unpack. */
+#define CCM_VLB_MAGIC 0x31564343u /* "CCV1" */
+#define CCM_VLB_INDEX_STRIDE 64
+uint64_t ccm_vlb_index_entries(uint64_t rows, uint64_t cols);
+ccm_status ccm_vlb_pack(const void* dense, int dtype, uint64_t rows, uint64_t cols,
+                        ccm_header* hdr, uint32_t* words, uint64_t capacity, uint64_t* index,
+                        void* ws, size_t ws_bytes, ccm_stream_t stream);
+ccm_status ccm_vlb_unpack(const ccm_header* hdr, const uint32_t* words, uint64_t capacity,
+                          const uint64_t* index, uint64_t rows, uint64_t cols, void* dense,
+                          int dtype, int32_t* err, ccm_stream_t stream);
 
 /* Matvec that allocates nothing (the paper has no counterpart; this is a
  * service of the library).  For callers that cannot hand ccm_matvec a device

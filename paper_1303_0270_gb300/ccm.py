@@ -17,7 +17,9 @@ from . import build as _build
 OK, E_INVAL, E_SHAPE, E_WIDTH, E_OVERFLOW, E_CAPACITY, E_RANGE, E_CUDA, E_TIMEOUT, E_INPUT = (
     0, -1, -2, -3, -4, -5, -6, -7, -8, -9)
 I32, I64 = 0, 1
-OP_MATVEC, OP_MATMUL, OP_PACK = 1, 2, 3
+OP_MATVEC, OP_MATMUL, OP_PACK, OP_VLB = 1, 2, 3, 4
+VLB_MAGIC = 0x31564343
+VLB_INDEX_STRIDE = 64
 MATMUL_AUTO, MATMUL_TENSOR, MATMUL_CUDACORE = 0, 1, 2
 MAGIC = 0x314D4343
 HEADER_WORDS = 16  # 64 bytes
@@ -70,8 +72,8 @@ SIGNATURES = {
     "ccm_pack": ([_vp, _i32, _u64, _u64, _MP, _vp, _sz, _vp], _i32),
     "ccm_unpack": ([_MP, _vp, _i32, _vp, _vp], _i32),
     "ccm_get": ([_MP, _vp, _u64, _vp, _vp, _vp], _i32),
-    "ccm_add": ([_MP, _MP, _MP, _vp], _i32),
-    "ccm_scale": ([_MP, _i64, _MP, _vp], _i32),
+    "ccm_add": ([_MP, _MP, _MP, _vp, _sz, _vp], _i32),
+    "ccm_scale": ([_MP, _i64, _MP, _vp, _sz, _vp], _i32),
     "ccm_matvec": ([_MP, _MP, _MP, _vp, _sz, _vp], _i32),
     "ccm_matmul": ([_MP, _MP, _MP, _i32, _vp, _sz, _vp], _i32),
     "ccm_workspace_bytes": ([_i32, _u64, _u64, _u64], _sz),
@@ -84,6 +86,9 @@ SIGNATURES = {
                         ctypes.POINTER(BatchInfo)], _i32),
     "ccm_batch_matvec": ([_vp, ctypes.POINTER(BatchInfo), _vp, _sz, _i32, _vp], _i32),
     "ccm_matvec_static": ([_MP, _MP, _MP, _vp], _i32),
+    "ccm_vlb_index_entries": ([_u64, _u64], _u64),
+    "ccm_vlb_pack": ([_vp, _i32, _u64, _u64, _vp, _vp, _u64, _vp, _vp, _sz, _vp], _i32),
+    "ccm_vlb_unpack": ([_vp, _vp, _u64, _vp, _u64, _u64, _vp, _i32, _vp, _vp], _i32),
     "ccm_launch_count": ([], _u64),
     "ccm_profile_next": ([_vp, _vp], _i32),
 }
@@ -300,10 +305,20 @@ def _bound_capacity(rows, cols, bound):
     return words_for(rows, cols, max(1, min(64, bound)))
 
 
-def add_into(a: PackedMatrix, b: PackedMatrix, c: PackedMatrix, stream=None) -> PackedMatrix:
+def _result_ws(c: PackedMatrix, ws, single_pass: bool):
+    if ws is None and single_pass:
+        nb = workspace_bytes(OP_PACK, c.rows, c.cols, c.capacity)
+        ws = torch.empty(nb, dtype=torch.uint8, device=c.device) if nb else None
+    return ws, (ctypes.c_void_p(ws.data_ptr()) if ws is not None else None), \
+        (ws.numel() if ws is not None else 0)
+
+
+def add_into(a: PackedMatrix, b: PackedMatrix, c: PackedMatrix, stream=None,
+             ws: torch.Tensor | None = None, single_pass: bool = True) -> PackedMatrix:
     ma, mb, mc = a.c(), b.c(), c.c()
-    _check(lib().ccm_add(ctypes.byref(ma), ctypes.byref(mb), ctypes.byref(mc), _stream(stream)),
-           "ccm_add")
+    ws, wsp, wsn = _result_ws(c, ws, single_pass)
+    _check(lib().ccm_add(ctypes.byref(ma), ctypes.byref(mb), ctypes.byref(mc), wsp, wsn,
+                         _stream(stream)), "ccm_add")
     c._written()
     return c
 
@@ -314,10 +329,12 @@ def add(a: PackedMatrix, b: PackedMatrix, capacity: int | None = None, stream=No
     return add_into(a, b, PackedMatrix(a.rows, a.cols, capacity, a.device), stream)
 
 
-def scale_into(a: PackedMatrix, s: int, c: PackedMatrix, stream=None) -> PackedMatrix:
+def scale_into(a: PackedMatrix, s: int, c: PackedMatrix, stream=None,
+               ws: torch.Tensor | None = None, single_pass: bool = True) -> PackedMatrix:
     ma, mc = a.c(), c.c()
-    _check(lib().ccm_scale(ctypes.byref(ma), int(s), ctypes.byref(mc), _stream(stream)),
-           "ccm_scale")
+    ws, wsp, wsn = _result_ws(c, ws, single_pass)
+    _check(lib().ccm_scale(ctypes.byref(ma), int(s), ctypes.byref(mc), wsp, wsn,
+                           _stream(stream)), "ccm_scale")
     c._written()
     return c
 
@@ -393,3 +410,89 @@ def gen_poisson(count: int, seed: int, stream_id: int, table: torch.Tensor, star
                                  ctypes.c_void_p(table.data_ptr()), table.numel(),
                                  _stream(stream)), "ccm_gen_poisson")
     return out
+
+
+# ---------------------------------------------------------------------------
+# VLB (Method 2): header + words + offset index, in one int32 buffer + index.
+# ---------------------------------------------------------------------------
+class VlbMatrix:
+    def __init__(self, rows: int, cols: int, capacity: int, device=None):
+        self.rows, self.cols, self.capacity = int(rows), int(cols), int(capacity)
+        dev = torch.device(device) if device is not None else torch.device("cuda")
+        self.buf = torch.empty(HEADER_WORDS + self.capacity, dtype=torch.int32, device=dev)
+        n_index = int(lib().ccm_vlb_index_entries(self.rows, self.cols))
+        self.index = torch.empty(n_index, dtype=torch.int64, device=dev)
+
+    @property
+    def device(self):
+        return self.buf.device
+
+    def header(self, stream=None) -> Header:
+        h = Header()
+        _check(lib().ccm_header_read(ctypes.c_void_p(self.buf.data_ptr()), ctypes.byref(h),
+                                     _stream(stream)), "ccm_header_read")
+        return h
+
+    def words(self) -> torch.Tensor:
+        return self.buf[HEADER_WORDS:HEADER_WORDS + int(self.header().nwords)]
+
+
+def vlb_measure(t: torch.Tensor, stream=None) -> Header:
+    """k, total bits and word count of the VLB stream of a dense matrix
+    (synchronous), without writing it."""
+    t, rows, cols, dt = _as_dense(t)
+    hdr = torch.empty(HEADER_WORDS, dtype=torch.int32, device=t.device)
+    ws = torch.empty(max(workspace_bytes(OP_VLB, rows, cols, 0), 256), dtype=torch.uint8,
+                     device=t.device)
+    _check(lib().ccm_vlb_pack(ctypes.c_void_p(t.data_ptr()), dt, rows, cols,
+                              ctypes.c_void_p(hdr.data_ptr()), None, 0, None,
+                              ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)),
+           "ccm_vlb_pack")
+    h = Header()
+    _check(lib().ccm_header_read(ctypes.c_void_p(hdr.data_ptr()), ctypes.byref(h),
+                                 _stream(stream)), "ccm_header_read")
+    return h
+
+
+def vlb_pack(t: torch.Tensor, capacity: int | None = None, stream=None) -> VlbMatrix:
+    t, rows, cols, dt = _as_dense(t)
+    if capacity is None:
+        h = vlb_measure(t, stream)
+        _check(h.status, "ccm_vlb_pack")
+        capacity = int(h.nwords)
+    out = VlbMatrix(rows, cols, capacity, t.device)
+    ws = torch.empty(max(workspace_bytes(OP_VLB, rows, cols, 0), 256), dtype=torch.uint8,
+                     device=t.device)
+    _check(lib().ccm_vlb_pack(ctypes.c_void_p(t.data_ptr()), dt, rows, cols,
+                              ctypes.c_void_p(out.buf.data_ptr()),
+                              ctypes.c_void_p(out.buf.data_ptr() + 4 * HEADER_WORDS), capacity,
+                              ctypes.c_void_p(out.index.data_ptr()),
+                              ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)),
+           "ccm_vlb_pack")
+    return out
+
+
+def vlb_unpack(v: VlbMatrix, dtype=torch.int64, stream=None, check: bool = True) -> torch.Tensor:
+    out = torch.empty((v.rows, v.cols), dtype=dtype, device=v.device)
+    err = torch.empty(1, dtype=torch.int32, device=v.device)
+    _check(lib().ccm_vlb_unpack(ctypes.c_void_p(v.buf.data_ptr()),
+                                ctypes.c_void_p(v.buf.data_ptr() + 4 * HEADER_WORDS), v.capacity,
+                                ctypes.c_void_p(v.index.data_ptr()), v.rows, v.cols,
+                                ctypes.c_void_p(out.data_ptr()), I64 if dtype == torch.int64 else I32,
+                                ctypes.c_void_p(err.data_ptr()), _stream(stream)), "ccm_vlb_unpack")
+    if check and v.rows * v.cols:
+        _check(int(err.item()), "ccm_vlb_unpack")
+    return out
+
+
+def choose(t: torch.Tensor, stream=None) -> dict:
+    """SM or VLB for this matrix: the bits each encoding needs (SM: n*b,
+    Eq. 15; VLB: sum of k + L_i, Eq. 16), measured on the GPU."""
+    t2, rows, cols, _ = _as_dense(t)
+    b, _ = measure(t2, stream)
+    v = vlb_measure(t2, stream)
+    sm_bits = rows * cols * b
+    vlb_bits = int(v.stat_or) if v.status == OK else None
+    best = "sm" if vlb_bits is None or sm_bits <= vlb_bits else "vlb"
+    return {"sm_bits": sm_bits, "vlb_bits": vlb_bits, "choice": best, "sm_width": b,
+            "vlb_prefix": int(v.width) if v.status == OK else None}

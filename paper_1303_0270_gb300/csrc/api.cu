@@ -98,21 +98,24 @@ ccm_status ccm_get(const ccm_matrix* a, const uint64_t* idx, uint64_t count, int
   return launched();
 }
 
-ccm_status ccm_add(const ccm_matrix* a, const ccm_matrix* b, const ccm_matrix* c,
-                   ccm_stream_t stream) {
+ccm_status ccm_add(const ccm_matrix* a, const ccm_matrix* b, const ccm_matrix* c, void* ws,
+                   size_t ws_bytes, ccm_stream_t stream) {
   if (!valid_in(a) || !valid_in(b) || !valid_out(c)) return CCM_E_INVAL;
   if (a->rows != b->rows || a->cols != b->cols || c->rows != a->rows || c->cols != a->cols)
     return CCM_E_SHAPE;
   if (!capacity_ok(c)) return CCM_E_CAPACITY;
-  ccm::run_add(*a, *b, *c, to_cuda(stream));
+  if (ws && reinterpret_cast<uintptr_t>(ws) % 256) return CCM_E_INVAL;
+  ccm::run_add(*a, *b, *c, ws, ws_bytes, to_cuda(stream));
   return launched();
 }
 
-ccm_status ccm_scale(const ccm_matrix* a, int64_t s, const ccm_matrix* c, ccm_stream_t stream) {
+ccm_status ccm_scale(const ccm_matrix* a, int64_t s, const ccm_matrix* c, void* ws,
+                     size_t ws_bytes, ccm_stream_t stream) {
   if (!valid_in(a) || !valid_out(c)) return CCM_E_INVAL;
   if (c->rows != a->rows || c->cols != a->cols) return CCM_E_SHAPE;
   if (!capacity_ok(c)) return CCM_E_CAPACITY;
-  ccm::run_scale(*a, s, *c, to_cuda(stream));
+  if (ws && reinterpret_cast<uintptr_t>(ws) % 256) return CCM_E_INVAL;
+  ccm::run_scale(*a, s, *c, ws, ws_bytes, to_cuda(stream));
   return launched();
 }
 
@@ -120,6 +123,7 @@ size_t ccm_workspace_bytes(int op, uint64_t m, uint64_t k, uint64_t n) {
   switch (op) {
     case CCM_OP_MATVEC: return ccm::matvec_workspace(m, k);
     case CCM_OP_PACK: return ccm::pack_workspace(m, k, n);
+    case CCM_OP_VLB: return ccm::vlb_workspace(m * k);
     case CCM_OP_MATMUL: return ccm::matmul_workspace_upper(m, k, n);
     default: return 0;
   }
@@ -148,6 +152,34 @@ ccm_status ccm_matmul(const ccm_matrix* a, const ccm_matrix* b, const ccm_matrix
   if (ws_bytes < ccm::matmul_workspace(*a, *b)) return CCM_E_CAPACITY;  // <= the shape bound
   int st = ccm::run_matmul(*a, *b, *c, path, ws, to_cuda(stream));
   if (st != CCM_OK) return (ccm_status)st;
+  return launched();
+}
+
+uint64_t ccm_vlb_index_entries(uint64_t rows, uint64_t cols) {
+  return (rows * cols + CCM_VLB_INDEX_STRIDE - 1) / CCM_VLB_INDEX_STRIDE + 1;
+}
+
+ccm_status ccm_vlb_pack(const void* dense, int dtype, uint64_t rows, uint64_t cols,
+                        ccm_header* hdr, uint32_t* words, uint64_t capacity, uint64_t* index,
+                        void* ws, size_t ws_bytes, ccm_stream_t stream) {
+  if (!hdr || !ws || (rows * cols && !dense)) return CCM_E_INVAL;
+  if (dtype != CCM_I32 && dtype != CCM_I64) return CCM_E_INVAL;
+  if (words && !index) return CCM_E_INVAL;
+  if (reinterpret_cast<uintptr_t>(hdr) % 16 || reinterpret_cast<uintptr_t>(ws) % 256)
+    return CCM_E_INVAL;
+  if (ws_bytes < ccm::vlb_workspace(rows * cols)) return CCM_E_CAPACITY;
+  ccm::run_vlb_pack(dense, dtype, rows, cols, hdr, words, capacity, index, ws, to_cuda(stream));
+  return launched();
+}
+
+ccm_status ccm_vlb_unpack(const ccm_header* hdr, const uint32_t* words, uint64_t capacity,
+                          const uint64_t* index, uint64_t rows, uint64_t cols, void* dense,
+                          int dtype, int32_t* err, ccm_stream_t stream) {
+  if (!hdr || (rows * cols && (!words || !index || !dense))) return CCM_E_INVAL;
+  if (dtype != CCM_I32 && dtype != CCM_I64) return CCM_E_INVAL;
+  if (rows * cols == 0) return CCM_OK;
+  ccm::run_vlb_unpack(hdr, words, capacity, index, rows, cols, dense, dtype, err,
+                      to_cuda(stream));
   return launched();
 }
 

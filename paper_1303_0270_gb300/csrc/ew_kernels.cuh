@@ -222,6 +222,78 @@ __global__ void __launch_bounds__(kThreads) k_ew(Op op, ccm_header* out, uint32_
   }
 }
 
+// Single-pass form of add / scale (with workspace): values are produced once,
+// each 1024-field tile is packed at its own width b_loc into its workspace
+// slot (slot_words apart) and the tile statistics are merged into the output
+// header; k_repack then writes the result at the matrix width b (a 16-byte
+// copy for every tile whose b_loc is already b).
+template <class Op, int BMAX>
+__global__ void __launch_bounds__(kThreads) k_ew_local(Op op, ccm_header* out,
+                                                       uint32_t* __restrict__ slots,
+                                                       uint32_t slot_words,
+                                                       uint8_t* __restrict__ tile_width,
+                                                       uint64_t n) {
+  using V = typename Op::template Val<BMAX>;
+  using U = typename std::make_unsigned<V>::type;
+  constexpr int kSignShift = 8 * sizeof(V) - 1;
+  __shared__ __align__(16) uint32_t s_buf[kWarps][kBufWords];
+  if (out->status != CCM_OK) return;
+  op.init(n);
+  const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+  uint32_t* buf = s_buf[warp];
+  const uint64_t ntiles = (n + kTile - 1) / kTile;
+  const uint64_t gwarps = (uint64_t)gridDim.x * kWarps;
+  uint64_t g_or = 0;
+  uint32_t g_neg = 0;
+  int ovf = 0;
+  uint64_t tile = (uint64_t)blockIdx.x * kWarps + warp;
+  typename Op::template Regs<BMAX> cur, nxt;
+  if (tile < ntiles) op.template prefetch<BMAX>(cur, tile, lane);
+  for (; tile < ntiles; tile += gwarps) {
+    if (tile + gwarps < ntiles) op.template prefetch<BMAX>(nxt, tile + gwarps, lane);
+    V val[32];
+    U orv = 0;
+    V negv = 0;
+    op.template produce<BMAX>(cur, buf, lane, ovf, [&](int k, V v) {
+      val[k] = v;
+      orv |= (U)(v ^ (v >> kSignShift));
+      negv |= v;
+    });
+    const uint64_t o = warp_or64((uint64_t)orv);
+    const uint32_t neg = __reduce_or_sync(0xffffffffu, (uint32_t)(negv < 0));
+    g_or |= o;
+    g_neg |= neg;
+    const int bl = width_from_stats(o, neg);
+    if (bl <= BMAX && bl <= 32) {
+      uint32_t u[32];
+      const uint32_t mask = bl >= 32 ? 0xffffffffu : ((1u << bl) - 1u);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) u[k] = (uint32_t)val[k] & mask;
+      encode_dispatch<BMAX>(bl, u, buf, lane);
+      __syncwarp();
+      uint4* dst = reinterpret_cast<uint4*>(slots + tile * (uint64_t)slot_words);
+      if (32 * bl <= (int)slot_words) {
+        for (int q = lane; q < 8 * bl; q += 32) {
+          const int w = 4 * q;
+          dst[q] = make_uint4(buf[stage_pos(w, bl)], buf[stage_pos(w + 1, bl)],
+                              buf[stage_pos(w + 2, bl)], buf[stage_pos(w + 3, bl)]);
+        }
+      }
+      __syncwarp();
+    }
+    if (lane == 0)
+      tile_width[tile] = (bl <= BMAX && 32 * bl <= (int)slot_words) ? (uint8_t)(bl | (neg ? 0x80 : 0))
+                                                                   : 0xFF;
+    cur = nxt;
+  }
+  ovf = (int)__reduce_or_sync(0xffffffffu, (uint32_t)ovf);
+  if (lane == 0) {
+    if (g_or) atomicOr(reinterpret_cast<unsigned long long*>(&out->stat_or), (unsigned long long)g_or);
+    if (g_neg) atomicOr(&out->stat_neg, 1u);
+    if (ovf) set_status(out, CCM_E_OVERFLOW);
+  }
+}
+
 // Pack pass of a dense int32/int64 matrix (its statistics come from k_stats).
 template <typename T, int BMAX>
 __global__ void __launch_bounds__(kThreads) k_pack_dense(const T* __restrict__ src,
@@ -265,6 +337,7 @@ template <typename T, int BMAX>
 __global__ void __launch_bounds__(kThreads) k_pack_local(const T* __restrict__ src,
                                                          ccm_header* out,
                                                          uint32_t* __restrict__ slots,
+                                                         uint32_t slot_words,
                                                          uint8_t* __restrict__ tile_width,
                                                          uint64_t n) {
   __shared__ __align__(16) uint32_t s_buf[kWarps][kBufWords];
@@ -295,14 +368,15 @@ __global__ void __launch_bounds__(kThreads) k_pack_local(const T* __restrict__ s
     g_or |= orv;
     g_neg |= neg;
     const int bl = width_from_stats(orv, neg);
-    if (bl <= BMAX) {
+    const bool fits = bl <= BMAX && 32 * bl <= (int)slot_words;
+    if (fits) {
       uint32_t u[32];
       const uint32_t mask = bl >= 32 ? 0xffffffffu : ((1u << bl) - 1u);
 #pragma unroll
       for (int k = 0; k < 32; ++k) u[k] = (uint32_t)v[k] & mask;
       encode_dispatch<BMAX>(bl, u, buf, lane);
       __syncwarp();
-      uint4* dst = reinterpret_cast<uint4*>(slots + tile * (uint64_t)(32 * BMAX));
+      uint4* dst = reinterpret_cast<uint4*>(slots + tile * (uint64_t)slot_words);
       for (int q = lane; q < 8 * bl; q += 32) {
         const int w = 4 * q;
         dst[q] = make_uint4(buf[stage_pos(w, bl)], buf[stage_pos(w + 1, bl)],
@@ -310,7 +384,7 @@ __global__ void __launch_bounds__(kThreads) k_pack_local(const T* __restrict__ s
       }
       __syncwarp();
     }
-    if (lane == 0) tile_width[tile] = bl <= BMAX ? (uint8_t)(bl | (neg ? 0x80 : 0)) : 0xFF;
+    if (lane == 0) tile_width[tile] = fits ? (uint8_t)(bl | (neg ? 0x80 : 0)) : 0xFF;
   }
   if (lane == 0) {
     if (g_or) atomicOr(reinterpret_cast<unsigned long long*>(&out->stat_or), (unsigned long long)g_or);
@@ -320,6 +394,7 @@ __global__ void __launch_bounds__(kThreads) k_pack_local(const T* __restrict__ s
 
 template <int BMAX>
 __global__ void __launch_bounds__(kThreads) k_repack(const uint32_t* __restrict__ slots,
+                                                     uint32_t slot_words,
                                                      const uint8_t* __restrict__ tile_width,
                                                      ccm_header* out, uint32_t* words,
                                                      uint64_t capacity, uint64_t n) {
@@ -335,7 +410,14 @@ __global__ void __launch_bounds__(kThreads) k_repack(const uint32_t* __restrict_
   for (uint64_t tile = (uint64_t)blockIdx.x * kWarps + warp; tile < ntiles; tile += gwarps) {
     const int tw = tile_width[tile];
     const int bl = tw & 0x7f, sl = tw >> 7;
-    const uint4* src = reinterpret_cast<const uint4*>(slots + tile * (uint64_t)(32 * BMAX));
+    const uint4* src = reinterpret_cast<const uint4*>(slots + tile * (uint64_t)slot_words);
+    if (bl == b && tile * (uint64_t)(32 * b) + 32 * b <= dw) {
+      // the tile is already at the matrix width: its bits are final (a value
+      // that fits b bits has the same low b bits signed or unsigned)
+      uint4* dst = reinterpret_cast<uint4*>(words + tile * (uint64_t)(32 * b));
+      for (int q = lane; q < 8 * b; q += 32) dst[q] = __ldg(src + q);
+      continue;
+    }
     for (int q = lane; q < 8 * bl; q += 32) {
       const uint4 v = __ldg(src + q);
       const int w = 4 * q;
@@ -355,6 +437,8 @@ __global__ void __launch_bounds__(kThreads) k_repack(const uint32_t* __restrict_
   }
 }
 
+// Workspace of the single-pass forms: one slot of 32*cls words per tile (cls
+// the output's width class), then one width byte per tile.
 inline size_t pack_ws_bytes(uint64_t n, int cls) {
   const uint64_t ntiles = (n + kTile - 1) / kTile;
   return ((ntiles * 32 * cls * 4 + 255) & ~(size_t)255) + ((ntiles + 255) & ~(size_t)255);
@@ -398,7 +482,7 @@ __global__ void __launch_bounds__(kThreads) k_unpack_ge(const ccm_header* h,
 // What the host asks one class to run.
 enum class EwKind {
   PackI64, PackI32, AddStats, AddPack, ScaleStats, ScalePack, UnpackI64, UnpackI32,
-  LocalI64, LocalI32, Repack
+  LocalI64, LocalI32, LocalAdd, LocalScale, Repack
 };
 
 struct EwCall {
@@ -415,6 +499,7 @@ struct EwCall {
   uint64_t rows, cols;
   int32_t* err;           // unpack status
   void* ws;               // Local* / Repack: workspace (slots, then tile widths)
+  int slot_class;         // Local* / Repack: width class of the output (slot = 32*class words)
 };
 
 inline int ew_grid(uint64_t n, int per_sm) {
@@ -462,19 +547,34 @@ void launch_ew_class(const EwCall& c, cudaStream_t st) {
       break;
     case EwKind::LocalI64:
     case EwKind::LocalI32:
+    case EwKind::LocalAdd:
+    case EwKind::LocalScale:
     case EwKind::Repack: {
       const uint64_t ntiles = (n + kTile - 1) / kTile;
+      const int sc = c.slot_class;
+      const uint32_t slot_words = (uint32_t)(32 * sc);
       uint32_t* slots = (uint32_t*)c.ws;
-      uint8_t* widths = (uint8_t*)c.ws + ((ntiles * 32 * C * 4 + 255) & ~(size_t)255);
+      uint8_t* widths = (uint8_t*)c.ws + ((ntiles * 32 * sc * 4 + 255) & ~(size_t)255);
       const int gl = ew_grid(n, 12);
       if (c.kind == EwKind::LocalI64)
         k_pack_local<int64_t, C><<<gl, kThreads, 0, st>>>((const int64_t*)c.dense, c.out, slots,
-                                                          widths, n);
+                                                          slot_words, widths, n);
       else if (c.kind == EwKind::LocalI32)
         k_pack_local<int32_t, C><<<gl, kThreads, 0, st>>>((const int32_t*)c.dense, c.out, slots,
-                                                          widths, n);
-      else
-        k_repack<C><<<gl, kThreads, 0, st>>>(slots, widths, c.out, c.words, c.capacity, n);
+                                                          slot_words, widths, n);
+      else if (c.kind == EwKind::LocalAdd)
+        k_ew_local<OpAdd, C><<<g, kThreads, 0, st>>>(OpAdd{a, b}, c.out, slots, slot_words,
+                                                     widths, n);
+      else if (c.kind == EwKind::LocalScale) {
+        if (c.s > -32768 && c.s < 32768)
+          k_ew_local<OpScale<true>, C><<<g, kThreads, 0, st>>>(OpScale<true>{a, c.s}, c.out, slots,
+                                                                slot_words, widths, n);
+        else
+          k_ew_local<OpScale<false>, C><<<g, kThreads, 0, st>>>(OpScale<false>{a, c.s}, c.out,
+                                                                 slots, slot_words, widths, n);
+      } else
+        k_repack<C><<<gl, kThreads, 0, st>>>(slots, slot_words, widths, c.out, c.words, c.capacity,
+                                             n);
       break;
     }
     case EwKind::UnpackI64:

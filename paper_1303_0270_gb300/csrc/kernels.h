@@ -28,8 +28,10 @@ void run_pack(const void* dense, int dtype, uint64_t rows, uint64_t cols, const 
 void run_unpack(const ccm_matrix& a, void* dense, int dtype, int32_t* err, cudaStream_t st);
 void run_get(const ccm_matrix& a, const uint64_t* idx, uint64_t count, int64_t* out, int32_t* err,
              cudaStream_t st);
-void run_add(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, cudaStream_t st);
-void run_scale(const ccm_matrix& a, int64_t s, const ccm_matrix& c, cudaStream_t st);
+void run_add(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, void* ws,
+             size_t ws_bytes, cudaStream_t st);
+void run_scale(const ccm_matrix& a, int64_t s, const ccm_matrix& c, void* ws, size_t ws_bytes,
+               cudaStream_t st);
 // Packs an int64 result held in scratch; `stats_done` when the producing
 // kernel has already merged the width statistics into out's header.
 void run_pack_scratch(const int64_t* vals, const ccm_matrix& out, cudaStream_t st,
@@ -45,6 +47,13 @@ size_t matmul_workspace(const ccm_matrix& a, const ccm_matrix& b);
 size_t matmul_workspace_upper(uint64_t m, uint64_t k, uint64_t n);
 int run_matmul(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, int path, void* ws,
                cudaStream_t st);
+
+size_t vlb_workspace(uint64_t n);
+void run_vlb_pack(const void* dense, int dtype, uint64_t rows, uint64_t cols, ccm_header* hdr,
+                  uint32_t* words, uint64_t capacity, uint64_t* index, void* ws, cudaStream_t st);
+void run_vlb_unpack(const ccm_header* hdr, const uint32_t* words, uint64_t capacity,
+                    const uint64_t* index, uint64_t rows, uint64_t cols, void* dense, int dtype,
+                    int32_t* err, cudaStream_t st);
 
 void run_gen_uniform(int64_t* out, uint64_t count, uint64_t seed, uint64_t stream_id,
                      uint64_t start, int64_t lo, int64_t hi, cudaStream_t st);

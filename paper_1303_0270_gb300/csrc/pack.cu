@@ -145,6 +145,7 @@ void run_pack(const void* dense, int dtype, uint64_t rows, uint64_t cols, const 
     c.rows = rows;
     c.cols = cols;
     c.ws = ws;
+    c.slot_class = cls;
     profile_begin(st);
     launch_ew(cls, c, st);
     profile_end(st);
@@ -280,7 +281,8 @@ void run_get(const ccm_matrix& a, const uint64_t* idx, uint64_t count, int64_t* 
 // ---------------------------------------------------------------------------
 // add / scale
 // ---------------------------------------------------------------------------
-void run_add(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, cudaStream_t st) {
+void run_add(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, void* ws,
+             size_t ws_bytes, cudaStream_t st) {
   InitArgs ia{};
   ia.out = c.hdr;
   ia.in0 = a.hdr;
@@ -297,6 +299,29 @@ void run_add(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, cuda
   uint64_t n = c.rows * c.cols;
   const int cls = ew_class(max(max(width_bound(a.capacity, n), width_bound(b.capacity, n)),
                                width_bound(c.capacity, n)));
+  const int out_cls = ew_class(width_bound(c.capacity, n));
+  if (cls && n && out_cls && ws && ws_bytes >= ge::pack_ws_bytes(n, out_cls)) {
+    // one pass over the inputs: tiles at their own width, then re-coded
+    ge::EwCall e{};
+    e.ha = a.hdr;
+    e.wa = a.words;
+    e.hb = b.hdr;
+    e.wb = b.words;
+    e.out = c.hdr;
+    e.words = c.words;
+    e.capacity = c.capacity;
+    e.rows = c.rows;
+    e.cols = c.cols;
+    e.ws = ws;
+    e.slot_class = out_cls;
+    e.kind = ge::EwKind::LocalAdd;
+    profile_begin(st);
+    launch_ew(cls, e, st);
+    profile_end(st);
+    e.kind = ge::EwKind::Repack;
+    launch_ew(cls, e, st);
+    return;
+  }
   if (cls && n) {
     ge::EwCall e{};
     e.ha = a.hdr;
@@ -323,7 +348,8 @@ void run_add(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, cuda
   profile_end(st);
 }
 
-void run_scale(const ccm_matrix& a, int64_t s, const ccm_matrix& c, cudaStream_t st) {
+void run_scale(const ccm_matrix& a, int64_t s, const ccm_matrix& c, void* ws, size_t ws_bytes,
+               cudaStream_t st) {
   InitArgs ia{};
   ia.out = c.hdr;
   ia.in0 = a.hdr;
@@ -335,6 +361,27 @@ void run_scale(const ccm_matrix& a, int64_t s, const ccm_matrix& c, cudaStream_t
   launch_init(ia, st);
   uint64_t n = c.rows * c.cols;
   const int cls = ew_class(max(width_bound(a.capacity, n), width_bound(c.capacity, n)));
+  const int out_cls = ew_class(width_bound(c.capacity, n));
+  if (cls && n && out_cls && ws && ws_bytes >= ge::pack_ws_bytes(n, out_cls)) {
+    ge::EwCall e{};
+    e.ha = a.hdr;
+    e.wa = a.words;
+    e.s = s;
+    e.out = c.hdr;
+    e.words = c.words;
+    e.capacity = c.capacity;
+    e.rows = c.rows;
+    e.cols = c.cols;
+    e.ws = ws;
+    e.slot_class = out_cls;
+    e.kind = ge::EwKind::LocalScale;
+    profile_begin(st);
+    launch_ew(cls, e, st);
+    profile_end(st);
+    e.kind = ge::EwKind::Repack;
+    launch_ew(cls, e, st);
+    return;
+  }
   if (cls && n) {
     ge::EwCall e{};
     e.ha = a.hdr;

@@ -54,15 +54,15 @@ def test_host_side_rejections_launch_nothing(L):
     bp = ctypes.byref
     a, b, c = _m(3, 4), _m(4, 3), _m(3, 4)
     # shape mismatch
-    assert L.ccm_add(bp(a), bp(b), bp(c), None) == ccm.E_SHAPE
+    assert L.ccm_add(bp(a), bp(b), bp(c), None, 0, None) == ccm.E_SHAPE
     # NULL header
     bad = _m(3, 4, hdr=0)
-    assert L.ccm_add(bp(bad), bp(a), bp(c), None) == ccm.E_INVAL
+    assert L.ccm_add(bp(bad), bp(a), bp(c), None, 0, None) == ccm.E_INVAL
     # misaligned header
-    assert L.ccm_scale(bp(_m(3, 4, hdr=0x1004)), 2, bp(c), None) == ccm.E_INVAL
+    assert L.ccm_scale(bp(_m(3, 4, hdr=0x1004)), 2, bp(c), None, 0, None) == ccm.E_INVAL
     # capacity below the width-1 minimum
     small = _m(30, 40, cap=4)
-    assert L.ccm_scale(bp(_m(30, 40)), 2, bp(small), None) == ccm.E_CAPACITY
+    assert L.ccm_scale(bp(_m(30, 40)), 2, bp(small), None, 0, None) == ccm.E_CAPACITY
     # pack: bad dtype, NULL dense, shape disagreement
     assert L.ccm_pack(ctypes.c_void_p(0x3000), 7, 3, 4, bp(c), None, 0, None) == ccm.E_INVAL
     assert L.ccm_pack(None, ccm.I64, 3, 4, bp(c), None, 0, None) == ccm.E_INVAL

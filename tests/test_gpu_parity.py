@@ -267,13 +267,18 @@ def test_width_class_and_runtime_kernels_agree(ccm, b):
     assert np.array_equal(ccm.unpack(pa_fast).cpu().numpy(), a)
     assert np.array_equal(ccm.unpack(pa_fast, dtype=torch.int32).cpu().numpy(), a)
     s_exp = oracle.add(oa, oc)
-    for cap in (s_exp.width, 64):
-        out = ccm.PackedMatrix(*shape, ccm.words_for(*shape, cap), device())
-        assert_same_packed(ccm.add_into(pa_fast, pc_fast, out), s_exp, f"add b={b} cap={cap}")
-    d_exp = oracle.scale(oa, -3)
-    for cap in (d_exp.width, 64):
-        out = ccm.PackedMatrix(*shape, ccm.words_for(*shape, cap), device())
-        assert_same_packed(ccm.scale_into(pa_fast, -3, out), d_exp, f"scale b={b} cap={cap}")
+    for cap in (s_exp.width, s_exp.width + 3, 64):
+        for single in (True, False):
+            out = ccm.PackedMatrix(*shape, ccm.words_for(*shape, cap), device())
+            assert_same_packed(ccm.add_into(pa_fast, pc_fast, out, single_pass=single), s_exp,
+                               f"add b={b} cap={cap} single={single}")
+    for s in (-3, 1 << 20):
+        d_exp = oracle.scale(oa, s)
+        for cap in (d_exp.width, 64):
+            for single in (True, False):
+                out = ccm.PackedMatrix(*shape, ccm.words_for(*shape, cap), device())
+                assert_same_packed(ccm.scale_into(pa_fast, s, out, single_pass=single), d_exp,
+                                   f"scale {s} b={b} cap={cap} single={single}")
 
 
 @pytest.mark.parametrize("m,n", [(1, 128), (31, 256), (300, 384), (257, 1280), (1000, 128)])
