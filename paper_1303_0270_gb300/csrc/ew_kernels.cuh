@@ -333,6 +333,37 @@ __global__ void __launch_bounds__(kThreads) k_pack_dense(const T* __restrict__ s
 // slot fits.  k_repack then re-codes each slot from b_loc to b (packed bytes
 // only, mostly from L2).  Dense traffic: one read instead of two.
 // ---------------------------------------------------------------------------
+// Dense int64 tiles are double-buffered with 16-byte cp.async (zero fill past
+// the end): the next tile is in flight while the warp packs the current one.
+// Shared layout: element f at f + 2*(f/32) (keeps 16-byte alignment; the
+// lane's 16-byte reads of its 32 elements are conflict-free).
+__device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, uint32_t bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_ge() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait1_ge() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait0_ge() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+constexpr int kDensePad = kTile + 2 * (kTile / 32);  // int64 slots per staged tile
+
+__device__ __forceinline__ void issue_dense_tile(int64_t* dst, const int64_t* __restrict__ src,
+                                                 uint64_t base, uint32_t nt, int lane) {
+#pragma unroll 4
+  for (int j = 0; j < kTile / 2 / 32; ++j) {
+    const uint32_t f = 2 * (lane + 32 * j);
+    const uint32_t valid = f + 2 <= nt ? 16u : (f < nt ? 8u : 0u);
+    cp_async16_zfill(dst + f + 2 * (f >> 5), src + base + (valid ? f : 0), valid);
+  }
+}
+
 template <typename T, int BMAX>
 __global__ void __launch_bounds__(kThreads) k_pack_local(const T* __restrict__ src,
                                                          ccm_header* out,
@@ -340,29 +371,64 @@ __global__ void __launch_bounds__(kThreads) k_pack_local(const T* __restrict__ s
                                                          uint32_t slot_words,
                                                          uint8_t* __restrict__ tile_width,
                                                          uint64_t n) {
-  __shared__ __align__(16) uint32_t s_buf[kWarps][kBufWords];
+  constexpr bool kPipe = sizeof(T) == 8;
+  constexpr int kStageWords = kPipe ? 2 * kDensePad : kBufWords;  // uint32 words per buffer
+  // dynamic: kWarps x (2 buffers for int64, 1 for int32) x kStageWords words
+  extern __shared__ __align__(16) uint32_t s_dyn[];
   if (out->status != CCM_OK) return;
   const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
-  uint32_t* buf = s_buf[warp];
-  T* tb = reinterpret_cast<T*>(buf);
+  uint32_t* buf0 = s_dyn + warp * (kPipe ? 2 * kStageWords : kBufWords);
   const uint64_t ntiles = (n + kTile - 1) / kTile;
   const uint64_t gwarps = (uint64_t)gridDim.x * kWarps;
   uint64_t g_or = 0;
   uint32_t g_neg = 0;
-  for (uint64_t tile = (uint64_t)blockIdx.x * kWarps + warp; tile < ntiles; tile += gwarps) {
+  uint64_t tile = (uint64_t)blockIdx.x * kWarps + warp;
+  int cur = 0;
+  if constexpr (kPipe) {
+    if (tile < ntiles)
+      issue_dense_tile(reinterpret_cast<int64_t*>(buf0), reinterpret_cast<const int64_t*>(src),
+                       tile * kTile, (uint32_t)umin((uint64_t)kTile, n - tile * kTile), lane);
+    cp_async_commit_ge();
+  }
+  for (; tile < ntiles; tile += gwarps) {
     const uint32_t nt = (uint32_t)umin((uint64_t)kTile, n - tile * kTile);
-    stage_dense<T>(tb, src, tile * kTile, nt, lane);
-    __syncwarp();
     int64_t v[32];
+    uint32_t* buf;  // where the packed words are staged
+    if constexpr (kPipe) {
+      const uint64_t next = tile + gwarps;
+      if (next < ntiles)
+        issue_dense_tile(reinterpret_cast<int64_t*>(buf0 + (cur ^ 1) * kStageWords),
+                         reinterpret_cast<const int64_t*>(src), next * kTile,
+                         (uint32_t)umin((uint64_t)kTile, n - next * kTile), lane);
+      cp_async_commit_ge();
+      cp_async_wait1_ge();
+      __syncwarp();
+      const int64_t* tb = reinterpret_cast<const int64_t*>(buf0 + cur * kStageWords);
+#pragma unroll
+      for (int k = 0; k < 32; k += 2) {
+        const longlong2 p = *reinterpret_cast<const longlong2*>(tb + 34 * lane + k);
+        v[k] = p.x;
+        v[k + 1] = p.y;
+      }
+      __syncwarp();
+      buf = buf0 + cur * kStageWords;  // the consumed tile's buffer stages the output
+      cur ^= 1;
+    } else {
+      T* tb = reinterpret_cast<T*>(buf0);
+      stage_dense<T>(tb, src, tile * kTile, nt, lane);
+      __syncwarp();
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] = (int64_t)tb[33 * lane + k];
+      __syncwarp();
+      buf = buf0;
+    }
     uint64_t orv = 0;
     uint32_t neg = 0;
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
-      v[k] = (int64_t)tb[33 * lane + k];
       orv |= fold(v[k]);
       neg |= (uint32_t)(v[k] < 0);
     }
-    __syncwarp();
     orv = warp_or64(orv);
     neg = __reduce_or_sync(0xffffffffu, neg);
     g_or |= orv;
@@ -386,6 +452,7 @@ __global__ void __launch_bounds__(kThreads) k_pack_local(const T* __restrict__ s
     }
     if (lane == 0) tile_width[tile] = fits ? (uint8_t)(bl | (neg ? 0x80 : 0)) : 0xFF;
   }
+  if constexpr (kPipe) cp_async_wait0_ge();
   if (lane == 0) {
     if (g_or) atomicOr(reinterpret_cast<unsigned long long*>(&out->stat_or), (unsigned long long)g_or);
     if (g_neg) atomicOr(&out->stat_neg, 1u);
@@ -556,12 +623,21 @@ void launch_ew_class(const EwCall& c, cudaStream_t st) {
       uint32_t* slots = (uint32_t*)c.ws;
       uint8_t* widths = (uint8_t*)c.ws + ((ntiles * 32 * sc * 4 + 255) & ~(size_t)255);
       const int gl = ew_grid(n, 12);
-      if (c.kind == EwKind::LocalI64)
-        k_pack_local<int64_t, C><<<gl, kThreads, 0, st>>>((const int64_t*)c.dense, c.out, slots,
-                                                          slot_words, widths, n);
-      else if (c.kind == EwKind::LocalI32)
-        k_pack_local<int32_t, C><<<gl, kThreads, 0, st>>>((const int32_t*)c.dense, c.out, slots,
-                                                          slot_words, widths, n);
+      if (c.kind == EwKind::LocalI64) {
+        const size_t smem = (size_t)kWarps * 2 * 2 * kDensePad * sizeof(uint32_t);
+        static bool attr = false;
+        if (!attr) {
+          cudaFuncSetAttribute(k_pack_local<int64_t, C>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+          attr = true;
+        }
+        k_pack_local<int64_t, C><<<gl, kThreads, smem, st>>>((const int64_t*)c.dense, c.out,
+                                                             slots, slot_words, widths, n);
+      } else if (c.kind == EwKind::LocalI32) {
+        const size_t smem = (size_t)kWarps * kBufWords * sizeof(uint32_t);
+        k_pack_local<int32_t, C><<<gl, kThreads, smem, st>>>((const int32_t*)c.dense, c.out,
+                                                             slots, slot_words, widths, n);
+      }
       else if (c.kind == EwKind::LocalAdd)
         k_ew_local<OpAdd, C><<<g, kThreads, 0, st>>>(OpAdd{a, b}, c.out, slots, slot_words,
                                                      widths, n);
