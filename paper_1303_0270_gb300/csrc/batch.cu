@@ -122,9 +122,20 @@ __device__ __noinline__ void run_unit(const Mat& M, const Unit& u, const int4* _
     const uint64_t end_bit = ((uint64_t)lrow * n + min(n, 32 * ls + 32)) * B;
     const uint32_t nwords = (uint32_t)(((end_bit + 31) >> 5) - w_first) + 1;
     const uint64_t dw = data_words((uint64_t)M.m * n, B);
-    for (uint32_t w = lane; w < nwords; w += 32) {
-      const uint64_t g = w_first + w;
-      stage[stage_pos((int)w, B)] = g < dw ? __ldg(M.wa + g) : 0u;
+    // the chunk's words, 8 loads in flight per lane before any is stored
+    for (uint32_t w0 = 0; w0 < nwords; w0 += 8 * 32) {
+      uint32_t tmp[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint32_t w = w0 + lane + 32 * j;
+        const uint64_t g = w_first + w;
+        tmp[j] = (w < nwords && g < dw) ? __ldg(M.wa + g) : 0u;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint32_t w = w0 + lane + 32 * j;
+        if (w < nwords) stage[stage_pos((int)w, B)] = tmp[j];
+      }
     }
     __syncwarp();
     long long acc = 0;

@@ -37,13 +37,23 @@ __device__ __forceinline__ void stage_packed(uint32_t* buf, const uint32_t* __re
   if (avail >= (uint64_t)tw && (w0 & 3) == 0) {
     // whole tile: 16-byte loads (the tile starts at byte 128*b*tile)
     const uint4* src = reinterpret_cast<const uint4*>(words + w0);
-    for (int q = lane; q < tw / 4; q += 32) {
-      uint4 v = __ldg(src + q);
-      int w = 4 * q;
-      buf[stage_pos(w, b)] = v.x;
-      buf[stage_pos(w + 1, b)] = v.y;
-      buf[stage_pos(w + 2, b)] = v.z;
-      buf[stage_pos(w + 3, b)] = v.w;
+    // all of the lane's 16-byte loads (at most 8: b <= 32) before any store
+    uint4 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int q = lane + 32 * j;
+      if (q < tw / 4) v[j] = __ldg(src + q);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int q = lane + 32 * j;
+      if (q < tw / 4) {
+        const int w = 4 * q;
+        buf[stage_pos(w, b)] = v[j].x;
+        buf[stage_pos(w + 1, b)] = v[j].y;
+        buf[stage_pos(w + 2, b)] = v[j].z;
+        buf[stage_pos(w + 3, b)] = v[j].w;
+      }
     }
   } else {
     for (int w = lane; w < tw; w += 32)

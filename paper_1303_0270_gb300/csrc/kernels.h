@@ -8,6 +8,7 @@
 namespace ccm {
 
 int num_sms();
+int max_smem_optin();  // shared memory a CTA may opt in to (bytes)
 
 // Largest width whose words fit `capacity` words for n fields (64 for n = 0):
 // a bound the host can compute although the width itself lives on the GPU.

@@ -98,6 +98,59 @@ int resident_ctas(int bmax, int threads, size_t smem) {
   return bmax <= 8 ? resident_ctas_8(threads, smem)
                    : bmax <= 16 ? resident_ctas_16(threads, smem) : resident_ctas_32(threads, smem);
 }
+namespace rows {
+// The x staging image, built once per call: for every 128-column chunk c,
+// x in dp4a byte order (144-byte rows) when b <= 8 and b_x <= 8, else int32
+// (528-byte rows); then one int per chunk, the sum of its x (the offset-binary
+// correction).  One CTA of 128 threads per chunk, grid-stride.
+__global__ void __launch_bounds__(128) k_xprep(const ccm_header* out, const ccm_header* ha,
+                                               const ccm_header* hx, const uint32_t* __restrict__ wx,
+                                               uint64_t n, uint8_t* __restrict__ img) {
+  __shared__ int s_part[4];
+  if (out->status != CCM_OK) return;
+  const int b = ha->width, bx = hx->width, sx = hx->is_signed;
+  const bool dp = b <= 8 && bx <= 8;
+  const uint32_t nchunks = (uint32_t)(n / kKC);
+  int* csum = reinterpret_cast<int*>(img + (uint64_t)nchunks * (dp ? kXPitch8 : kXPitch32));
+  const uint32_t f = threadIdx.x;
+  for (uint32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const int v = (int)decode_field(wx, (uint64_t)c * kKC + f, bx, sx);
+    if (dp)
+      img[(uint64_t)c * kXPitch8 + x8_pos_rt(f, b)] = (uint8_t)v;
+    else
+      reinterpret_cast<int*>(img + (uint64_t)c * kXPitch32)[f] = v;
+    int sum = v;
+    for (int d = 16; d; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
+    if (f % 32 == 0) s_part[f / 32] = sum;
+    __syncthreads();
+    if (f == 0) csum[c] = s_part[0] + s_part[1] + s_part[2] + s_part[3];
+    __syncthreads();
+  }
+}
+
+int resident_ctas_8(int threads, size_t smem);
+int resident_ctas_16(int threads, size_t smem);
+int resident_ctas_32(int threads, size_t smem);
+void launch_8(const RowArgs& a, bool narrow, unsigned grid, int threads, size_t smem,
+              cudaStream_t st);
+void launch_16(const RowArgs& a, bool narrow, unsigned grid, int threads, size_t smem,
+               cudaStream_t st);
+void launch_32(const RowArgs& a, bool narrow, unsigned grid, int threads, size_t smem,
+               cudaStream_t st);
+int resident_ctas(int bmax, int threads, size_t smem) {
+  return bmax <= 8 ? resident_ctas_8(threads, smem)
+                   : bmax <= 16 ? resident_ctas_16(threads, smem) : resident_ctas_32(threads, smem);
+}
+void launch(int bmax, const RowArgs& a, bool narrow, unsigned grid, int threads, size_t smem,
+            cudaStream_t st) {
+  if (bmax <= 8)
+    launch_8(a, narrow, grid, threads, smem, st);
+  else if (bmax <= 16)
+    launch_16(a, narrow, grid, threads, smem, st);
+  else
+    launch_32(a, narrow, grid, threads, smem, st);
+}
+}  // namespace rows
 }  // namespace mvf
 
 size_t matvec_workspace(uint64_t m, uint64_t n) {
@@ -128,36 +181,110 @@ void run_matvec(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& y, v
     ia.zero_count = m;
   }
   const int bmax_a = width_bound(a.capacity, m * n), bmax_x = width_bound(x.capacity, n);
-  const bool fast = m && n && n % mvf::kKC == 0 && bmax_a <= 32 && bmax_x <= 31 &&
-                    bmax_a + bmax_x + bitlen_host(n) <= 63;
-  if (fast) ia.zero_ptr = yv, ia.zero_count = m;
-  launch_init(ia, st);
-  if (fast) {
-    const int warps = bmax_a <= 12 ? 8 : 4;
+  // Streaming kernels: row-aligned A (cols % 128 == 0), fields of at most 32
+  // bits, x of at most 31, and every partial sum inside int64.
+  const bool aligned = m && n && n % mvf::kKC == 0 && bmax_a <= 32 && bmax_x <= 31 &&
+                       bmax_a + bmax_x + bitlen_host(n) <= 63;
+  const bool narrow = bmax_a + bmax_x + 7 <= 31;
+  // Row-streaming kernel when all of x fits in shared memory beside the
+  // rings: CTAs of 8 or 4 warps, whichever keeps more warps resident.
+  struct RowPlan {
+    int warps = 0;
+    unsigned grid = 0;
+    size_t smem = 0;
+    uint64_t resident_warps = 0;
+  } rplan;
+  if (aligned) {
+    const bool bytes = bmax_a <= 8 && bmax_x <= 8;
+    const uint64_t xr = (mvf::rows::x_region_bytes(n, bytes) + 15) & ~(uint64_t)15;
+    const uint32_t wr = mvf::warp_region_bytes(bmax_a);
+    const uint64_t nchunks = n / mvf::kKC;
+    const uint64_t T = m * ((nchunks + mvf::rows::kChunksPerStage - 1) /
+                            mvf::rows::kChunksPerStage);
+    for (int w : {8, 4}) {
+      const uint64_t smem = (uint64_t)w * wr + xr;
+      if (smem > (uint64_t)max_smem_optin()) continue;
+      const int per_sm = mvf::rows::resident_ctas(bmax_a, w * 32, (size_t)smem);
+      if (per_sm <= 0) continue;
+      const uint64_t need = (T + w - 1) / w;
+      const uint64_t grid = umin((uint64_t)num_sms() * per_sm, need);
+      const uint64_t rw = grid * w;
+      if (rw > rplan.resident_warps) {
+        rplan.warps = w;
+        rplan.grid = (unsigned)grid;
+        rplan.smem = (size_t)smem;
+        rplan.resident_warps = rw;
+      }
+    }
+  }
+  const bool use_rows = rplan.warps > 0;
+  // (the slab kernel addresses a warp's 32 rows with 32-bit offsets)
+  bool fast = !use_rows && aligned && n * (uint64_t)bmax_a < (1ull << 30);
+  // Launch plan for CTAs of `warps` warps: one wave of as many CTAs as stay
+  // resident; column slabs split the work when there are fewer row blocks
+  // than that, CTAs loop over row blocks when there are more.  A slab's x
+  // (int32) must fit in shared memory beside the stage rings.
+  struct Plan {
+    int warps;
+    uint64_t grid_x, splits, per, resident_warps;
+    size_t smem;
+  };
+  const uint32_t warp_region = mvf::warp_region_bytes(bmax_a);
+  const uint64_t groups = n / mvf::kKC;  // 128-column groups
+  auto make_plan = [&](int warps) {
+    Plan p{warps, 0, 0, 0, 0, 0};
+    const size_t stage_region = (size_t)warps * warp_region;
+    const size_t cap = (size_t)max_smem_optin();
+    if (stage_region + mvf::kKC * sizeof(int) > cap) return p;
+    const uint64_t per_cap = (cap - stage_region) / (mvf::kKC * sizeof(int));
     const uint64_t row_blocks = (m + 32 * warps - 1) / (32 * warps);
-    const uint64_t groups = n / mvf::kKC;  // 128-column groups
-    const size_t stage_region = (size_t)warps * mvf::kStages * 32 * mvf::pitch_bytes(bmax_a);
-    // one wave: as many CTAs as stay resident; column slabs split the work
-    // when there are fewer row blocks than that, CTAs loop over row blocks
-    // when there are more
     const int per_sm0 = mvf::resident_ctas(bmax_a, warps * 32,
                                            stage_region + umin(n, 1024) * sizeof(int));
     const uint64_t resident0 = (uint64_t)num_sms() * (uint64_t)(per_sm0 > 0 ? per_sm0 : 1);
     uint64_t splits = umin(umax(resident0 / umax(row_blocks, 1), 1), groups);
     splits = umin(splits, 65535);
-    const uint64_t per = (groups + splits - 1) / splits;
-    splits = (groups + per - 1) / per;
-    const int per_sm = mvf::resident_ctas(bmax_a, warps * 32,
-                                          stage_region + per * mvf::kKC * sizeof(int));
+    p.per = umin((groups + splits - 1) / splits, per_cap);
+    p.splits = (groups + p.per - 1) / p.per;
+    p.smem = stage_region + p.per * mvf::kKC * sizeof(int);
+    const int per_sm = mvf::resident_ctas(bmax_a, warps * 32, p.smem);
     const uint64_t resident = (uint64_t)num_sms() * (uint64_t)(per_sm > 0 ? per_sm : 1);
-    const uint64_t grid_x = umin(row_blocks, umax(resident / splits, 1));
-    mvf::Args args{y.hdr, a.hdr, a.words, x.hdr, x.words, m, n,
-                   (uint32_t)(per * mvf::kKC), 0u, yv};
-    args.stage_region = (uint32_t)stage_region;
-    const size_t smem = args.stage_region + per * mvf::kKC * sizeof(int);
-    dim3 grid((unsigned)grid_x, (unsigned)splits);
+    p.grid_x = umin(row_blocks, umax(resident / p.splits, 1));
+    p.resident_warps = umin(p.grid_x * p.splits, resident) * warps;
+    return p;
+  };
+  Plan plan{};
+  if (fast) {
+    plan = make_plan(8);
+    const Plan p4 = make_plan(4);
+    if (p4.resident_warps > plan.resident_warps) plan = p4;
+    fast = plan.per > 0;
+  }
+  if (fast || use_rows) ia.zero_ptr = yv, ia.zero_count = m;
+  launch_init(ia, st);
+  if (use_rows) {
+    uint8_t* img = reinterpret_cast<uint8_t*>(xs);  // n * 8 bytes >= the image
+    const unsigned gx = (unsigned)umin(n / mvf::kKC, (uint64_t)num_sms() * 8);
+    mvf::rows::k_xprep<<<gx, mvf::kKC, 0, st>>>(y.hdr, a.hdr, x.hdr, x.words, n, img);
+    note_launch();
+    mvf::rows::RowArgs ra{y.hdr, a.hdr, a.words, x.hdr, x.words, m, n, 0u, 0u, yv, img};
+    ra.warp_region = mvf::warp_region_bytes(bmax_a);
+    ra.x_offset = (uint32_t)((size_t)rplan.warps * ra.warp_region);
     profile_begin(st);
-    const bool narrow = bmax_a + bmax_x + 7 <= 31;
+    mvf::rows::launch(bmax_a, ra, narrow, rplan.grid, rplan.warps * 32, rplan.smem, st);
+    profile_end(st);
+    note_launch();
+    run_pack_scratch(yv, y, st);
+    return;
+  }
+  if (fast) {
+    const int warps = plan.warps;
+    mvf::Args args{y.hdr, a.hdr, a.words, x.hdr, x.words, m, n,
+                   (uint32_t)(plan.per * mvf::kKC), 0u, 0u, yv};
+    args.stage_region = (uint32_t)((size_t)warps * warp_region);
+    args.warp_region = warp_region;
+    const size_t smem = plan.smem;
+    dim3 grid((unsigned)plan.grid_x, (unsigned)plan.splits);
+    profile_begin(st);
     if (bmax_a <= 8)
       mvf::launch_matvec_fast8(args, narrow, grid, warps * 32, smem, st);
     else if (bmax_a <= 16)

@@ -54,6 +54,18 @@ int num_sms() {
   return cached;
 }
 
+int max_smem_optin() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  static int cached_dev = -1, cached = 0;
+  if (dev != cached_dev) {
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cached = v > 0 ? v : 48 * 1024;
+    cached_dev = dev;
+  }
+  return cached;
+}
+
 __global__ void k_init(InitArgs a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     int st = CCM_OK;

@@ -295,6 +295,59 @@ def test_matvec_row_aligned(ccm, m, n, ba, bx, sa):
     assert_same_packed(y, o, f"matvec aligned {m}x{n} b={ba}/{bx}")
 
 
+def _x_kind(seed, n, kind):
+    if kind == "s8":
+        return _rand(seed, (n, 1), 8)
+    if kind == "u7":
+        return _rand(seed, (n, 1), 7, False)
+    if kind == "u8":  # does not fit int8: the int32 path
+        return _rand(seed, (n, 1), 8, False)
+    return _rand(seed, (n, 1), 9)  # "s9", likewise
+
+
+@pytest.mark.parametrize("ba", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("sa", [0, 1])
+@pytest.mark.parametrize("xk", ["s8", "u7", "u8", "s9"])
+def test_matvec_byte_lanes(ccm, ba, sa, xk):
+    """Widths <= 8 with x in int8: the dp4a byte-lane path (offset binary for
+    signed fields, x permuted for the widths 1, 2, 4), against the oracle; x
+    that does not fit int8 takes the int32 path of the same kernel.  257 rows
+    (a ragged last row block) by 1280 columns (several column slabs)."""
+    m, n = 257, 1280
+    a = _rand(ba * 31 + sa, (m, n), ba, bool(sa))
+    x = _x_kind(ba + 7 * sa, n, xk)
+    o = oracle.matvec(oracle.pack(a), oracle.pack(x))
+    px = ccm.pack(to_dev(x))
+    for cap in (ba, 16, 32):  # the width-class kernels for 8, 16 and 32 bits
+        pa = _pack_cap(ccm, a, cap)
+        y = ccm.matvec(pa, px, capacity=ccm.words_for(m, 1, 64))
+        assert_same_packed(y, o, f"matvec byte lanes b={ba} s={sa} x={xk} cap={cap}")
+
+
+@pytest.mark.parametrize("ba,sa", [(5, 0), (4, 1), (8, 1), (3, 1)])
+def test_matvec_byte_lanes_large(ccm, ba, sa):
+    """2048 x 8192 (64 stages per row, long slabs): byte-lane path."""
+    m, n = 2048, 8192
+    a = _rand(ba * 131 + sa, (m, n), ba, bool(sa))
+    x = _rand(n, (n, 1), 8)
+    o = oracle.matvec(oracle.pack(a), oracle.pack(x))
+    y = ccm.matvec(ccm.pack(to_dev(a)), ccm.pack(to_dev(x)))
+    assert_same_packed(y, o, f"matvec byte lanes {m}x{n} b={ba} s={sa}")
+
+
+@pytest.mark.parametrize("m,n,ba,sa,xk", [(3, 262144, 5, 0, "s8"), (3, 262144, 3, 1, "s8"),
+                                         (2, 262144, 4, 1, "u7"), (5, 65536, 12, 1, "s9"),
+                                         (33, 131072, 8, 0, "u8")])
+def test_matvec_long_rows(ccm, m, n, ba, sa, xk):
+    """Rows too long for x to sit in shared memory whole: the column-slab
+    kernel (x staged per slab, partial sums added per slab)."""
+    a = _rand(n + ba, (m, n), ba, bool(sa))
+    x = _x_kind(n + 1, n, xk)
+    o = oracle.matvec(oracle.pack(a), oracle.pack(x))
+    y = ccm.matvec(ccm.pack(to_dev(a)), ccm.pack(to_dev(x)), capacity=ccm.words_for(m, 1, 64))
+    assert_same_packed(y, o, f"matvec long rows {m}x{n} b={ba} s={sa} x={xk}")
+
+
 # ---------------------------------------------------------------------------
 # Tensor-core matmul (exact 4-bit digit decomposition, e4m3 x e4m3 -> f32)
 # ---------------------------------------------------------------------------
