@@ -315,19 +315,21 @@ def run_gpu(args, rank, world, local_rank):
     hbm, peak_kind = peaks()
     kernels = {"pack": "ge::k_pack_local<int64_t, 8>", "unpack": "ge::k_unpack_ge<int64_t, 8>",
                "add": "ge::k_ew<OpAdd, 8, pack>", "scale": "ge::k_ew<OpScale<true>, 16, pack>",
-               "matvec": "mvf::k_matvec_fast<8, narrow>"}
+               "matvec": "mvf::k_matvec_rows<8, narrow>"}
     per_op = {}
     for k, t in kern_ms.items():
         gbs = ops[k] / (t * 1e-3) / 1e9
         per_op[k] = {"kernel": kernels[k], "ms": round(t, 5), "algorithmic_bytes": int(ops[k]),
                      "GB/s": round(gbs, 1), "frac_of_hbm": round(gbs / hbm, 3)}
+    def roofline(d):
+        return {"bound": "hbm", "kernel": d["kernel"], "achieved": d["GB/s"], "peak": hbm,
+                "unit": "GB/s", "frac": round(d["GB/s"] / hbm, 4),
+                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                "traffic": kernel_traffic(d["kernel"]),
+                "algorithmic_bytes_per_launch": d["algorithmic_bytes"]}
     dom = max(per_op, key=lambda k: per_op[k]["ms"])
-    d = per_op[dom]
-    roof = {"bound": "hbm", "kernel": d["kernel"], "achieved": d["GB/s"], "peak": hbm,
-            "unit": "GB/s", "frac": round(d["GB/s"] / hbm, 4),
-            "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
-            "traffic": kernel_traffic(d["kernel"]),
-            "algorithmic_bytes_per_launch": d["algorithmic_bytes"]}
+    roof = roofline(per_op[dom])
+    roof_mv = roofline(per_op["matvec"]) if "matvec" in per_op else None
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
@@ -342,9 +344,25 @@ def run_gpu(args, rank, world, local_rank):
         "step_bytes": int(step_bytes), "per_op": per_op,
         "matvec_GBps": per_op.get("matvec", {}).get("GB/s"),
         "eta1_vs_int64": round((64 - widths["A"][0]) / 64, 4),
-        "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        "roofline": roof, "roofline_matvec": roof_mv,
+        # two events recorded back to back on the stream: the floor inside
+        # every per-kernel time above (reported, not subtracted)
+        "event_pair_floor_us": event_pair_floor(torch),
+        "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
     }
     return line
+
+
+def event_pair_floor(torch, reps: int = 50) -> float:
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1e3)
+    return round(statistics.mean(ts), 2)
 
 
 def run_batch(args, rank, world, local_rank):

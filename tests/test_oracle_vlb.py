@@ -40,6 +40,28 @@ def test_vlb_round_trip_brute_force():
             assert oracle.vlb_unpack(v).tolist() == list(combo)
 
 
+def _stream_by_strings(values):
+    """The VLB stream spelled out as text: for each entry its bit length L in
+    k prefix bits, then the entry in L bits, each least significant bit first
+    (the stream convention of Method 1, carried over to Method 2)."""
+    lens = [max(1, int(v).bit_length()) for v in values]
+    k = max(lens).bit_length()
+    bits = ""
+    for v, L in zip(values, lens):
+        bits += format(L, f"0{k}b")[::-1] + format(int(v), f"0{L}b")[::-1]
+    return k, bits
+
+
+def test_vlb_stream_against_string_construction():
+    for n in range(1, 5):
+        for combo in itertools.product(range(0, 9), repeat=n):
+            v = oracle.vlb_pack(np.array(combo))
+            k, bits = _stream_by_strings(combo)
+            assert (v.k, v.nbits) == (k, len(bits))
+            got = "".join(format(int(w), "032b")[::-1] for w in v.words)
+            assert got[:len(bits)] == bits and set(got[len(bits):]) <= {"0"}
+
+
 def test_vlb_size_matches_eq16():
     rng = np.random.default_rng(3)
     for _ in range(50):
