@@ -519,6 +519,105 @@ def run_matmul_bench(args, rank, world, local_rank):
             "results": results}
 
 
+def run_vlb_bench(args, rank, world, local_rank):
+    """VLB (Method 2) against SM (Method 1) on two 8192 x 8192 matrices: the
+    Poisson(5) count matrix of the default step (SM is smaller) and a heavy
+    tailed one with bit lengths spread over 1..40 (VLB is smaller).  Times the
+    encoder (dense int64 -> VLB stream + index), the decoder and the matvec on
+    the VLB stream, with the SM pack and matvec beside them; y compared word
+    for word between the two encodings."""
+    import ctypes
+
+    import torch
+
+    import synth
+    from paper_1303_0270_gb300 import ccm
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    n_rows = n_cols = 8192
+    n = n_rows * n_cols
+    hbm, _ = peaks()
+    table = torch.from_numpy(synth.poisson_cdf_table(LAMBDA))
+    X = ccm.gen_uniform(n_cols, SEED_A, synth.STREAM_X, -128, 127, device=dev).view(n_cols, 1)
+    px = ccm.pack(X)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def kernel_ms(fn, reps):
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0.record()
+        k1.record()
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for i in range(reps):
+            flush.fill_(i & 255)  # inputs out of L2 between repetitions
+            ccm.profile_next(k0, k1)
+            fn()
+            torch.cuda.synchronize()
+            ts.append(k0.elapsed_time(k1))
+        return statistics.mean(ts)
+
+    results = []
+    for name in ("poisson5", "heavy_tail_1_40"):
+        if name == "poisson5":
+            A = ccm.gen_poisson(n, SEED_A, synth.STREAM_A, table, device=dev).view(n_rows, n_cols)
+        else:  # floor(2^(40 u)), u uniform: bit lengths spread evenly over 1..40
+            U = ccm.gen_uniform(n, SEED_A, synth.STREAM_A, 0, (1 << 53) - 1, device=dev)
+            A = torch.floor(torch.exp2(U.double() * (40.0 / 2 ** 53))).long().view(n_rows, n_cols)
+            del U
+        choice = ccm.choose(A)
+        sm_b = choice["sm_width"]
+        pa = ccm.PackedMatrix(n_rows, n_cols, ccm.words_for(n_rows, n_cols, sm_b), dev)
+        ws_pack = ccm.workspace(ccm.OP_PACK, n_rows, n_cols, pa.capacity, dev)
+        v = ccm.vlb_pack(A)
+        vbytes = 4 * int(v.header().nwords)
+        y_sm = ccm.PackedMatrix(n_rows, 1, ccm.words_for(n_rows, 1, 64), dev)
+        y_v = ccm.PackedMatrix(n_rows, 1, ccm.words_for(n_rows, 1, 64), dev)
+        ws_mv = ccm.workspace(ccm.OP_MATVEC, n_rows, n_cols, 1, dev)
+        ws_vmv = ccm.workspace(ccm.OP_VLB_MATVEC, n_rows, n_cols, 0, dev)
+        ws_v = torch.empty(max(ccm.workspace_bytes(ccm.OP_VLB, n_rows, n_cols, 0), 256),
+                           dtype=torch.uint8, device=dev)
+        dense_out = torch.empty_like(A)
+        reps = max(args.steps, 3)
+        L = ccm.lib()
+        vp = ctypes.c_void_p
+
+        def vlb_encode():
+            L.ccm_vlb_pack(vp(A.data_ptr()), ccm.I64, n_rows, n_cols, vp(v.buf.data_ptr()),
+                           vp(v.buf.data_ptr() + 4 * ccm.HEADER_WORDS), v.capacity,
+                           vp(v.index.data_ptr()), vp(ws_v.data_ptr()), ws_v.numel(),
+                           vp(torch.cuda.current_stream().cuda_stream))
+
+        t = {
+            "sm_pack": kernel_ms(lambda: ccm.pack_into(A, pa, ws=ws_pack), reps),
+            "sm_matvec": kernel_ms(lambda: ccm.matvec_into(pa, px, y_sm, ws=ws_mv), reps),
+            "vlb_encode": kernel_ms(vlb_encode, reps),
+            "vlb_decode": kernel_ms(lambda: ccm.vlb_unpack(v, check=False), reps),
+            "vlb_matvec": kernel_ms(lambda: ccm.vlb_matvec_into(v, px, y_v, ws=ws_vmv), reps),
+        }
+        same = (y_sm.check().width == y_v.check().width and
+                torch.equal(y_sm.words(), y_v.words()))
+        assert torch.equal(ccm.vlb_unpack(v), A), "VLB round trip"
+        sm_bytes = n * sm_b / 8
+        gbs = {"sm_pack": (8 * n + sm_bytes), "sm_matvec": sm_bytes,
+               "vlb_encode": 8 * n + vbytes,  # the write pass (k_vlb_write): dense in, stream out
+               "vlb_decode": vbytes + 8 * n, "vlb_matvec": vbytes}
+        results.append({
+            "matrix": name, "sm_bits_per_entry": sm_b,
+            "vlb_bits_per_entry": round(8 * vbytes / n, 3), "vlb_prefix_bits": choice["vlb_prefix"],
+            "choice": choice["choice"], "y_identical_sm_vs_vlb": bool(same),
+            "kernel_ms": {k: round(val, 4) for k, val in t.items()},
+            "GB/s": {k: round(gbs[k] / (t[k] * 1e-3) / 1e9, 1) for k in t},
+        })
+        del A, dense_out, v, pa
+        torch.cuda.empty_cache()
+    mv = results[1]["GB/s"]["vlb_matvec"]
+    return {"metric": METRIC, "workload": "vlb codec", "unit": "GB/s",
+            "value": mv, "value_is": "VLB matvec, heavy-tailed matrix, stream bytes / kernel time",
+            "frac_of_hbm": round(mv / hbm, 4), "l2": "flushed (256 MiB write) before every repetition",
+            "results": results}
+
+
 def run_serve_bench(args, rank, world, local_rank):
     """Serving: a store of packed matrices (dims log-uniform in [64, 8192),
     widths U{2..20}) resident on the GPU, a Poisson stream of requests (60 %
@@ -695,7 +794,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ccm", choices=["ccm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="step", choices=["step", "batch", "matmul", "serve"])
+    ap.add_argument("--workload", default="step",
+                    choices=["step", "batch", "matmul", "serve", "vlb"])
     ap.add_argument("--store-gb", type=float, default=8.0)
     ap.add_argument("--serve-budget-gb", type=float, default=16.0)
     ap.add_argument("--serve-requests", type=int, default=2000)
@@ -719,8 +819,9 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    if args.workload in ("batch", "matmul", "serve"):
-        fn = {"batch": run_batch, "matmul": run_matmul_bench, "serve": run_serve_bench}[args.workload]
+    if args.workload in ("batch", "matmul", "serve", "vlb"):
+        fn = {"batch": run_batch, "matmul": run_matmul_bench, "serve": run_serve_bench,
+              "vlb": run_vlb_bench}[args.workload]
         line = fn(args, rank, world, local_rank)
         if rank == 0:
             print(json.dumps(line), flush=True)

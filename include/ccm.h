@@ -111,7 +111,8 @@ typedef enum ccm_op {
   CCM_OP_MATVEC = 1,
   CCM_OP_MATMUL = 2,
   CCM_OP_PACK = 3,
-  CCM_OP_VLB = 4
+  CCM_OP_VLB = 4,
+  CCM_OP_VLB_MATVEC = 5
 } ccm_op;
 
 /* Matmul paths. */
@@ -291,6 +292,20 @@ ccm_status ccm_vlb_pack(const void* dense, int dtype, uint64_t rows, uint64_t co
 ccm_status ccm_vlb_unpack(const ccm_header* hdr, const uint32_t* words, uint64_t capacity,
                           const uint64_t* index, uint64_t rows, uint64_t cols, void* dense,
                           int dtype, int32_t* err, ccm_stream_t stream);
+
+/* y = A x with A (rows x cols) in VLB form -- the operation of Introduction
+ * ("computable": work on the compressed matrix) on Method 2's encoding: each
+ * entry is decoded from the stream as it is used (the index locates every
+ * 64th entry), never stored densely.  x and y are SM matrices as for
+ * ccm_matvec (x: cols x 1, y: rows x 1, y re-packed at its exact width).
+ * `ws`: ccm_workspace_bytes(CCM_OP_VLB_MATVEC, rows, cols, 0) bytes,
+ * 256-byte aligned.  Errors as for ccm_matvec; a VLB header that does not
+ * match (rows, cols, capacity) or a stream that ends early: CCM_E_INPUT in
+ * y's header. */
+ccm_status ccm_vlb_matvec(const ccm_header* hdr, const uint32_t* words, uint64_t capacity,
+                          const uint64_t* index, uint64_t rows, uint64_t cols,
+                          const ccm_matrix* x, const ccm_matrix* y, void* ws, size_t ws_bytes,
+                          ccm_stream_t stream);
 
 /* Matvec that allocates nothing (the paper has no counterpart; this is a
  * service of the library).  For callers that cannot hand ccm_matvec a device

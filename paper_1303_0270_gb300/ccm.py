@@ -17,7 +17,7 @@ from . import build as _build
 OK, E_INVAL, E_SHAPE, E_WIDTH, E_OVERFLOW, E_CAPACITY, E_RANGE, E_CUDA, E_TIMEOUT, E_INPUT = (
     0, -1, -2, -3, -4, -5, -6, -7, -8, -9)
 I32, I64 = 0, 1
-OP_MATVEC, OP_MATMUL, OP_PACK, OP_VLB = 1, 2, 3, 4
+OP_MATVEC, OP_MATMUL, OP_PACK, OP_VLB, OP_VLB_MATVEC = 1, 2, 3, 4, 5
 VLB_MAGIC = 0x31564343
 VLB_INDEX_STRIDE = 64
 MATMUL_AUTO, MATMUL_TENSOR, MATMUL_CUDACORE = 0, 1, 2
@@ -89,6 +89,7 @@ SIGNATURES = {
     "ccm_vlb_index_entries": ([_u64, _u64], _u64),
     "ccm_vlb_pack": ([_vp, _i32, _u64, _u64, _vp, _vp, _u64, _vp, _vp, _sz, _vp], _i32),
     "ccm_vlb_unpack": ([_vp, _vp, _u64, _vp, _u64, _u64, _vp, _i32, _vp, _vp], _i32),
+    "ccm_vlb_matvec": ([_vp, _vp, _u64, _vp, _u64, _u64, _MP, _MP, _vp, _sz, _vp], _i32),
     "ccm_launch_count": ([], _u64),
     "ccm_profile_next": ([_vp, _vp], _i32),
 }
@@ -483,6 +484,29 @@ def vlb_unpack(v: VlbMatrix, dtype=torch.int64, stream=None, check: bool = True)
     if check and v.rows * v.cols:
         _check(int(err.item()), "ccm_vlb_unpack")
     return out
+
+
+def vlb_matvec_into(v: VlbMatrix, x: PackedMatrix, y: PackedMatrix,
+                    ws: torch.Tensor | None = None, stream=None) -> PackedMatrix:
+    """y = A x with A in VLB form (decoded entry by entry as it is used)."""
+    if ws is None:
+        ws = workspace(OP_VLB_MATVEC, v.rows, v.cols, 0, v.device)
+    mx, my = x.c(), y.c()
+    _check(lib().ccm_vlb_matvec(ctypes.c_void_p(v.buf.data_ptr()),
+                                ctypes.c_void_p(v.buf.data_ptr() + 4 * HEADER_WORDS), v.capacity,
+                                ctypes.c_void_p(v.index.data_ptr()), v.rows, v.cols,
+                                ctypes.byref(mx), ctypes.byref(my), ctypes.c_void_p(ws.data_ptr()),
+                                ws.numel(), _stream(stream)), "ccm_vlb_matvec")
+    y._written()
+    return y
+
+
+def vlb_matvec(v: VlbMatrix, x: PackedMatrix, capacity: int | None = None,
+               stream=None) -> PackedMatrix:
+    if capacity is None:
+        capacity = words_for(v.rows, 1, 64)
+    y = PackedMatrix(v.rows, 1, capacity, v.device)
+    return vlb_matvec_into(v, x, y, stream=stream)
 
 
 def choose(t: torch.Tensor, stream=None) -> dict:

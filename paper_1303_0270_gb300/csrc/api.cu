@@ -124,6 +124,7 @@ size_t ccm_workspace_bytes(int op, uint64_t m, uint64_t k, uint64_t n) {
     case CCM_OP_MATVEC: return ccm::matvec_workspace(m, k);
     case CCM_OP_PACK: return ccm::pack_workspace(m, k, n);
     case CCM_OP_VLB: return ccm::vlb_workspace(m * k);
+    case CCM_OP_VLB_MATVEC: return ccm::vlb_matvec_workspace(m);
     case CCM_OP_MATMUL: return ccm::matmul_workspace_upper(m, k, n);
     default: return 0;
   }
@@ -180,6 +181,20 @@ ccm_status ccm_vlb_unpack(const ccm_header* hdr, const uint32_t* words, uint64_t
   if (rows * cols == 0) return CCM_OK;
   ccm::run_vlb_unpack(hdr, words, capacity, index, rows, cols, dense, dtype, err,
                       to_cuda(stream));
+  return launched();
+}
+
+ccm_status ccm_vlb_matvec(const ccm_header* hdr, const uint32_t* words, uint64_t capacity,
+                          const uint64_t* index, uint64_t rows, uint64_t cols,
+                          const ccm_matrix* x, const ccm_matrix* y, void* ws, size_t ws_bytes,
+                          ccm_stream_t stream) {
+  if (!hdr || !ws || !valid_in(x) || !valid_out(y)) return CCM_E_INVAL;
+  if (rows * cols && (!words || !index)) return CCM_E_INVAL;
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return CCM_E_INVAL;
+  if (x->rows != cols || x->cols != 1 || y->rows != rows || y->cols != 1) return CCM_E_SHAPE;
+  if (!capacity_ok(y)) return CCM_E_CAPACITY;
+  if (ws_bytes < ccm::vlb_matvec_workspace(rows)) return CCM_E_CAPACITY;
+  ccm::run_vlb_matvec(hdr, words, capacity, index, rows, cols, *x, *y, ws, to_cuda(stream));
   return launched();
 }
 

@@ -50,6 +50,10 @@ int run_matmul(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, in
                cudaStream_t st);
 
 size_t vlb_workspace(uint64_t n);
+size_t vlb_matvec_workspace(uint64_t rows);
+void run_vlb_matvec(const ccm_header* hdr, const uint32_t* words, uint64_t capacity,
+                    const uint64_t* index, uint64_t rows, uint64_t cols, const ccm_matrix& x,
+                    const ccm_matrix& y, void* ws, cudaStream_t st);
 void run_vlb_pack(const void* dense, int dtype, uint64_t rows, uint64_t cols, ccm_header* hdr,
                   uint32_t* words, uint64_t capacity, uint64_t* index, void* ws, cudaStream_t st);
 void run_vlb_unpack(const ccm_header* hdr, const uint32_t* words, uint64_t capacity,

@@ -232,6 +232,39 @@ __device__ __forceinline__ uint64_t read_bits(const uint32_t* __restrict__ w, ui
   return len >= 64 ? r : (r & ((1ull << len) - 1ull));
 }
 
+// Sequential reader of the stream from a bit position: a 64-bit buffer
+// refilled one 32-bit word at a time (one load per 32 bits consumed).
+struct BitReader {
+  const uint32_t* __restrict__ w;
+  uint64_t buf;
+  uint64_t next;  // index of the next word to load
+  int have;       // valid bits in buf
+  __device__ __forceinline__ BitReader(const uint32_t* words, uint64_t pos) : w(words) {
+    const uint64_t wi = pos / 32;
+    const int s = (int)(pos % 32);
+    buf = (uint64_t)__ldg(w + wi) >> s;
+    have = 32 - s;
+    next = wi + 1;
+  }
+  // the next len (<= 32) bits
+  __device__ __forceinline__ uint32_t take(int len) {
+    if (have < len) {
+      buf |= (uint64_t)__ldg(w + next++) << have;
+      have += 32;
+    }
+    const uint32_t v = (uint32_t)(buf & ((1ull << len) - 1ull));
+    buf >>= len;
+    have -= len;
+    return v;
+  }
+  // the next len (1..64) bits
+  __device__ __forceinline__ uint64_t take64(int len) {
+    if (len <= 32) return take(len);
+    const uint64_t lo = take(32);
+    return lo | ((uint64_t)take(len - 32) << 32);
+  }
+};
+
 // A valid VLB header for the expected shape and buffer.
 __device__ __forceinline__ int check_vlb(const ccm_header* hdr, uint64_t rows, uint64_t cols,
                                          uint64_t capacity) {
@@ -261,15 +294,85 @@ __global__ void __launch_bounds__(256) k_vlb_unpack(const ccm_header* hdr,
     uint64_t pos = index[c];
     const uint64_t limit = hdr->stat_or;  // total bits: never read past the stream
     const uint64_t e_end = umin(n, (c + 1) * kStride);
+    BitReader br(words, pos);
     for (uint64_t e = c * kStride; e < e_end; ++e) {
       if (pos + k > limit) break;
-      const int L = (int)read_bits(words, pos, k);
-      if (L < 1 || pos + k + L > limit) break;
-      const uint64_t v = read_bits(words, pos + k, L);
-      out[e] = (T)v;
+      const int L = (int)br.take(k);
+      if (L < 1 || L > 64 || pos + k + L > limit) break;
+      out[e] = (T)br.take64(L);
       pos += k + L;
     }
   }
+}
+
+// y = A x with A in VLB form: one warp per row; lane l takes the 64-entry
+// index blocks l, l + 32, ... that overlap the row, decodes them from the
+// block's indexed bit offset (skipping the entries before the row start) and
+// accumulates a_ij * x_j in 128 bits; the warp's sum is checked against the
+// int64 range and stored in the int64 y scratch.  x is read straight from
+// its packed form.
+__device__ __forceinline__ __int128 shfl_xor_i128(__int128 v, int d) {
+  uint64_t lo = (uint64_t)v, hi = (uint64_t)((unsigned __int128)v >> 64);
+  lo = __shfl_xor_sync(0xffffffffu, lo, d);
+  hi = __shfl_xor_sync(0xffffffffu, hi, d);
+  return (__int128)(((unsigned __int128)hi << 64) | lo);
+}
+
+__global__ void __launch_bounds__(256) k_vlb_matvec(const ccm_header* hdr,
+                                                    const uint32_t* __restrict__ words,
+                                                    const uint64_t* __restrict__ index,
+                                                    uint64_t rows, uint64_t cols,
+                                                    uint64_t capacity, ccm_header* out,
+                                                    const ccm_header* hx,
+                                                    const uint32_t* __restrict__ wx,
+                                                    int64_t* __restrict__ y) {
+  if (out->status != CCM_OK) return;
+  const int st = check_vlb(hdr, rows, cols, capacity);
+  if (st != CCM_OK) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_status(out, st);
+    return;
+  }
+  const int k = hdr->width;
+  const int bx = hx->width, sx = hx->is_signed;
+  const uint64_t limit = hdr->stat_or;  // total bits: never read past the stream
+  // every partial sum inside int64 when (largest L) + b_x + bitlen(cols) <= 63
+  const bool narrow = (int)hdr->reserved0 + bx + bitlen64(cols) <= 63;
+  const int lane = threadIdx.x % 32;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+  int bad = 0, ovf = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; i < rows;
+       i += warps) {
+    const uint64_t rs = i * cols, re = rs + cols;
+    __int128 acc = 0;
+    for (uint64_t c = rs / kStride + lane; c * kStride < re; c += 32) {
+      uint64_t pos = index[c];
+      const uint64_t e_end = umin(re, (c + 1) * kStride);
+      BitReader br(words, pos);
+      long long acc64 = 0;
+      for (uint64_t e = c * kStride; e < e_end; ++e) {
+        if (pos + k > limit) { bad = 1; break; }
+        const int L = (int)br.take(k);
+        if (L < 1 || L > 64 || pos + k + L > limit) { bad = 1; break; }
+        const uint64_t v = br.take64(L);
+        if (e >= rs) {
+          const int64_t xj = decode_field(wx, e - rs, bx, sx);
+          if (narrow)
+            acc64 += (long long)v * xj;
+          else
+            acc += (__int128)(int64_t)v * (__int128)xj;
+        }
+        pos += k + L;
+      }
+      acc += acc64;
+    }
+    for (int d = 16; d; d >>= 1) acc += shfl_xor_i128(acc, d);
+    if (lane == 0) {
+      if (acc < -((__int128)1 << 63) || acc >= ((__int128)1 << 63)) ovf = 1;
+      y[i] = (int64_t)acc;
+    }
+  }
+  if (bad) set_status(out, CCM_E_INPUT);
+  if (ovf) set_status(out, CCM_E_OVERFLOW);
 }
 
 }  // namespace vlb
@@ -328,6 +431,38 @@ void run_vlb_unpack(const ccm_header* hdr, const uint32_t* words, uint64_t capac
                                                    (int32_t*)dense, err);
   profile_end(st);
   note_launch();
+}
+
+}  // namespace ccm
+
+namespace ccm {
+
+size_t vlb_matvec_workspace(uint64_t rows) { return ((rows * 8 + 255) & ~(size_t)255) + 256; }
+
+void run_vlb_matvec(const ccm_header* hdr, const uint32_t* words, uint64_t capacity,
+                    const uint64_t* index, uint64_t rows, uint64_t cols, const ccm_matrix& x,
+                    const ccm_matrix& y, void* ws, cudaStream_t st) {
+  int64_t* yv = (int64_t*)ws;
+  InitArgs ia{};
+  ia.out = y.hdr;
+  ia.in0 = x.hdr;
+  ia.in0_rows = x.rows;
+  ia.in0_cols = x.cols;
+  ia.in0_capacity = x.capacity;
+  ia.out_rows = y.rows;
+  ia.out_cols = y.cols;
+  ia.zero_ptr = yv;
+  ia.zero_count = rows;
+  launch_init(ia, st);
+  if (rows && cols) {
+    const int g = (int)umin((rows + 7) / 8, (uint64_t)num_sms() * 8);
+    profile_begin(st);
+    vlb::k_vlb_matvec<<<g, 256, 0, st>>>(hdr, words, index, rows, cols, capacity, y.hdr, x.hdr,
+                                         x.words, yv);
+    profile_end(st);
+    note_launch();
+  }
+  run_pack_scratch(yv, y, st);
 }
 
 }  // namespace ccm

@@ -80,6 +80,18 @@ def test_host_side_rejections_launch_nothing(L):
     need = L.ccm_workspace_bytes(ccm.OP_MATMUL, 3, 4, 3)
     assert L.ccm_matmul(bp(a), bp(b), bp(_m(3, 3)), 9, ws, need, None) == ccm.E_INVAL
     assert L.ccm_matmul(bp(a), bp(a), bp(_m(3, 4)), 0, ws, need, None) == ccm.E_SHAPE
+    # VLB matvec: NULL stream pointers, x / y shapes, workspace size and alignment
+    h = ctypes.c_void_p(0x5000)
+    need = L.ccm_workspace_bytes(ccm.OP_VLB_MATVEC, 3, 4, 0)
+    assert need >= 3 * 8
+    assert L.ccm_vlb_matvec(h, None, 8, ctypes.c_void_p(0x6000), 3, 4, bp(x), bp(y), ws, need,
+                            None) == ccm.E_INVAL
+    assert L.ccm_vlb_matvec(h, ctypes.c_void_p(0x7000), 8, ctypes.c_void_p(0x6000), 3, 4,
+                            bp(_m(5, 1)), bp(y), ws, need, None) == ccm.E_SHAPE
+    assert L.ccm_vlb_matvec(h, ctypes.c_void_p(0x7000), 8, ctypes.c_void_p(0x6000), 3, 4,
+                            bp(x), bp(y), ws, need - 1, None) == ccm.E_CAPACITY
+    assert L.ccm_vlb_matvec(h, ctypes.c_void_p(0x7000), 8, ctypes.c_void_p(0x6000), 3, 4,
+                            bp(x), bp(y), ctypes.c_void_p(0x10010), need, None) == ccm.E_INVAL
     # generators
     assert L.ccm_gen_uniform(None, 5, 1, 0, 0, 0, 1, None) == ccm.E_INVAL
     assert L.ccm_gen_uniform(ctypes.c_void_p(0x4000), 5, 1, 0, 0, 3, 1, None) == ccm.E_INVAL

@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import device, lib_ccm, to_dev, torch
+from gpu_util import assert_same_packed, device, lib_ccm, to_dev, torch, words_np
 
 pytestmark = pytest.mark.gpu
 
@@ -62,3 +62,35 @@ def test_choose_matches_the_two_sizes(ccm):
         assert c["sm_bits"] == arr.size * oracle.pack(arr).width
         assert c["vlb_bits"] == oracle.vlb_pack(arr).nbits
         assert c["choice"] == ("sm" if c["sm_bits"] <= c["vlb_bits"] else "vlb")
+
+
+@pytest.mark.parametrize("rows,cols,kind", [(1, 1, "poisson"), (7, 64, "poisson"), (13, 100, "poisson"),
+                                            (257, 1280, "poisson"), (33, 4096, "wide"),
+                                            (64, 63, "wide"), (5, 3000, "zeros")])
+def test_vlb_matvec_matches_oracle(ccm, rows, cols, kind):
+    """y = A x with A in VLB form against the oracle (A decoded by the oracle's
+    VLB unpack, multiplied, y re-packed): word for word."""
+    n = rows * cols
+    if kind == "poisson":
+        a = synth.count_matrix(rows + cols, synth.STREAM_A, rows, cols)
+    elif kind == "wide":  # bit lengths spread over 1..40 (the prefix needs 6 bits)
+        u = synth.u53(synth.u64(rows, synth.STREAM_A, 0, n))
+        a = np.floor(2.0 ** (u * 40)).astype(np.int64).reshape(rows, cols)
+    else:
+        a = np.zeros((rows, cols), dtype=np.int64)
+    x = synth.uniform_int(cols, synth.STREAM_X, cols, -128, 127).reshape(cols, 1)
+    ov = oracle.vlb_pack(a.ravel())
+    expect = oracle.matvec(oracle.pack(oracle.vlb_unpack(ov).reshape(rows, cols)), oracle.pack(x))
+    v = ccm.vlb_pack(to_dev(a))
+    y = ccm.vlb_matvec(v, ccm.pack(to_dev(x)))
+    assert_same_packed(y, expect, f"vlb matvec {rows}x{cols} {kind}")
+    # the SM route gives the same y
+    ys = ccm.matvec(ccm.pack(to_dev(a)), ccm.pack(to_dev(x)), capacity=y.capacity)
+    assert np.array_equal(words_np(ys), words_np(y))
+
+
+def test_vlb_matvec_overflow_is_reported(ccm):
+    a = np.full((2, 8), (1 << 62) - 1, dtype=np.int64)
+    x = np.full((8, 1), 3, dtype=np.int64)
+    y = ccm.vlb_matvec(ccm.vlb_pack(to_dev(a)), ccm.pack(to_dev(x)))
+    assert y.status == ccm.E_OVERFLOW
