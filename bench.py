@@ -183,9 +183,6 @@ class Workload:
                             ctypes.c_void_p(self.got.data_ptr()),
                             ctypes.c_void_p(self.err.data_ptr() + 4), st))
         prof("add")
-        # add/scale: the two-pass route (statistics, then pack) measured faster
-        # here than the single-pass one (whose re-code pass cannot copy tiles
-        # when the sum is one bit wider than most tiles)
         rc.append(L.ccm_add(by(self.ma), by(self.mb), by(self.mc), None, 0, st))
         prof("scale")
         rc.append(L.ccm_scale(by(self.ma), SCALE, by(self.md), None, 0, st))
@@ -314,7 +311,8 @@ def run_gpu(args, rank, world, local_rank):
         return None
     hbm, peak_kind = peaks()
     kernels = {"pack": "ge::k_pack_local<int64_t, 8>", "unpack": "ge::k_unpack_ge<int64_t, 8>",
-               "add": "ge::k_ew<OpAdd, 8, pack>", "scale": "ge::k_ew<OpScale<true>, 16, pack>",
+               "add": "ge::k_ew<OpAdd, 8, spec> + finish",
+               "scale": "ge::k_ew<OpScale<true>, 16, spec> + finish",
                "matvec": "mvf::k_matvec_rows<8, narrow>"}
     per_op = {}
     for k, t in kern_ms.items():

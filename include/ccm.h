@@ -172,14 +172,17 @@ ccm_status ccm_get(const ccm_matrix* a, const uint64_t* idx, uint64_t count, int
 
 /* C = A + B, exact, entrywise; A, B and C have the same shape; A and B may
  * have different widths and sign modes.  C is re-packed at its own width.
- * `ws` (optional, as for ccm_pack: ccm_workspace_bytes(CCM_OP_PACK, rows,
- * cols, c->capacity) bytes) lets the inputs be decoded once instead of twice;
- * NULL takes the two-pass route.  The result is the same either way. */
+ * One pass writes C at the width the input ranges bound the sum to; a second
+ * pass re-packs only when the exact width is smaller (and when that bound
+ * needs more than c->capacity words).  `ws`, `ws_bytes`: not used (any
+ * value, NULL included). */
 ccm_status ccm_add(const ccm_matrix* a, const ccm_matrix* b, const ccm_matrix* c, void* ws,
                    size_t ws_bytes, ccm_stream_t stream);
 
 /* C = s * A for an int64 scalar s, exact; CCM_E_OVERFLOW when an entry does
- * not fit int64.  C is re-packed at its own width.  `ws` as for ccm_add. */
+ * not fit int64.  C is re-packed at its own width, in one pass when s times
+ * the range of A's width is the result's exact width, as for ccm_add.
+ * `ws`, `ws_bytes`: not used. */
 ccm_status ccm_scale(const ccm_matrix* a, int64_t s, const ccm_matrix* c, void* ws,
                      size_t ws_bytes, ccm_stream_t stream);
 
@@ -339,7 +342,8 @@ ccm_status ccm_matvec_static(const ccm_matrix* a, const ccm_matrix* x, const ccm
  * cudaEventRecord(stop) after it, on that call's stream, so the caller can
  * time that one kernel with cudaEventElapsedTime.  `start` and `stop` are
  * cudaEvent_t handles owned by the caller; NULL, NULL cancels.  The main
- * kernel is: k_pack for ccm_pack/ccm_add/ccm_scale, k_stats for ccm_measure,
+ * kernel is: k_pack for ccm_pack, the two passes of ccm_add/ccm_scale
+ * (together), k_stats for ccm_measure,
  * k_unpack, k_get, and the product kernel of ccm_matvec/ccm_matmul. */
 uint64_t ccm_launch_count(void);
 ccm_status ccm_profile_next(void* start_event, void* stop_event);

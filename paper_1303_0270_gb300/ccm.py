@@ -306,19 +306,9 @@ def _bound_capacity(rows, cols, bound):
     return words_for(rows, cols, max(1, min(64, bound)))
 
 
-def _result_ws(c: PackedMatrix, ws, single_pass: bool):
-    if ws is None and single_pass:
-        nb = workspace_bytes(OP_PACK, c.rows, c.cols, c.capacity)
-        ws = torch.empty(nb, dtype=torch.uint8, device=c.device) if nb else None
-    return ws, (ctypes.c_void_p(ws.data_ptr()) if ws is not None else None), \
-        (ws.numel() if ws is not None else 0)
-
-
-def add_into(a: PackedMatrix, b: PackedMatrix, c: PackedMatrix, stream=None,
-             ws: torch.Tensor | None = None, single_pass: bool = True) -> PackedMatrix:
+def add_into(a: PackedMatrix, b: PackedMatrix, c: PackedMatrix, stream=None) -> PackedMatrix:
     ma, mb, mc = a.c(), b.c(), c.c()
-    ws, wsp, wsn = _result_ws(c, ws, single_pass)
-    _check(lib().ccm_add(ctypes.byref(ma), ctypes.byref(mb), ctypes.byref(mc), wsp, wsn,
+    _check(lib().ccm_add(ctypes.byref(ma), ctypes.byref(mb), ctypes.byref(mc), None, 0,
                          _stream(stream)), "ccm_add")
     c._written()
     return c
@@ -330,12 +320,10 @@ def add(a: PackedMatrix, b: PackedMatrix, capacity: int | None = None, stream=No
     return add_into(a, b, PackedMatrix(a.rows, a.cols, capacity, a.device), stream)
 
 
-def scale_into(a: PackedMatrix, s: int, c: PackedMatrix, stream=None,
-               ws: torch.Tensor | None = None, single_pass: bool = True) -> PackedMatrix:
+def scale_into(a: PackedMatrix, s: int, c: PackedMatrix, stream=None) -> PackedMatrix:
     ma, mc = a.c(), c.c()
-    ws, wsp, wsn = _result_ws(c, ws, single_pass)
-    _check(lib().ccm_scale(ctypes.byref(ma), int(s), ctypes.byref(mc), wsp, wsn,
-                           _stream(stream)), "ccm_scale")
+    _check(lib().ccm_scale(ctypes.byref(ma), int(s), ctypes.byref(mc), None, 0, _stream(stream)),
+           "ccm_scale")
     c._written()
     return c
 

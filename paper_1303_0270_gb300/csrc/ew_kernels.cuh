@@ -11,6 +11,14 @@
 // packed inputs recompute their values in the pack pass instead of keeping
 // them: re-reading b-bit inputs costs less than writing and reading int64.
 //
+// Add and scale first try one pass: the input headers bound the result to a
+// range (for add, the sum of the two ranges; for scale, s times the range
+// of A) and so to a width b_spec; the statistics pass also writes every
+// field at b_spec.  When the exact width turns out to be b_spec -- the usual
+// case: the bound is reached as soon as one pair of entries is near its
+// extremes -- the pack pass only finalises the header; otherwise it re-packs
+// at the exact width as above.
+//
 // Memory-level parallelism: a warp loads the words of its next tile into
 // registers (16-byte loads) while it decodes the current one, so every warp
 // keeps one tile of every input in flight.
@@ -86,6 +94,19 @@ struct PackedIn {
 
 constexpr int kRegion = kBufWords / 2;  // 1056 words: one packed tile of width <= 32
 
+// The values a b-bit field can hold (b <= 63).
+__device__ __forceinline__ int64_t range_lo(int b, int sgn) { return sgn ? -(1ll << (b - 1)) : 0; }
+__device__ __forceinline__ int64_t range_hi(int b, int sgn) {
+  return sgn ? (1ll << (b - 1)) - 1 : (1ll << b) - 1;
+}
+// The width (Eq. 1, two's complement when lo < 0) of the values [lo, hi].
+__device__ __forceinline__ int range_width(int64_t lo, int64_t hi) {
+  const int h = bitlen64((uint64_t)(hi > 0 ? hi : 0));
+  if (lo >= 0) return h > 1 ? h : 1;
+  const int l = bitlen64((uint64_t)~lo);
+  return 1 + (h > l ? h : l);
+}
+
 // ---------------------------------------------------------------------------
 // Operations.  produce() hands every field value of the lane's group to
 // sink(k, value) as Val<BMAX> (int32 when the class bounds every value below
@@ -105,6 +126,12 @@ struct OpAdd {
   __device__ __forceinline__ void init(uint64_t n) {
     a.init(n);
     b.init(n);
+  }
+  // Width of [lo_a + lo_b, hi_a + hi_b] (widths of at most 32 bits here).
+  __device__ __forceinline__ int spec_width() const {
+    const int64_t lo = range_lo(a.b, a.sgn) + range_lo(b.b, b.sgn);
+    const int64_t hi = range_hi(a.b, a.sgn) + range_hi(b.b, b.sgn);
+    return range_width(lo, hi);
   }
   template <int BMAX>
   __device__ __forceinline__ void prefetch(Regs<BMAX>& r, uint64_t tile, int lane) const {
@@ -145,6 +172,18 @@ struct OpScale {
     TileRegs<BMAX> ra;
   };
   __device__ __forceinline__ void init(uint64_t n) { a.init(n); }
+  // Width of s times the range of A (65 when that leaves int64).
+  __device__ __forceinline__ int spec_width() const {
+    __int128 lo = (__int128)range_lo(a.b, a.sgn) * s, hi = (__int128)range_hi(a.b, a.sgn) * s;
+    if (lo > hi) {
+      const __int128 t = lo;
+      lo = hi;
+      hi = t;
+    }
+    const __int128 lim = (__int128)1 << 62;
+    if (lo < -lim || hi >= lim) return 65;
+    return range_width((int64_t)lo, (int64_t)hi);
+  }
   template <int BMAX>
   __device__ __forceinline__ void prefetch(Regs<BMAX>& r, uint64_t tile, int lane) const {
     a.load(r.ra, tile, lane);
@@ -166,24 +205,38 @@ struct OpScale {
   }
 };
 
-// Statistics (PACK = false) or pack (PACK = true) pass of add / scale.
-template <class Op, int BMAX, bool PACK>
+// Pass of add / scale: statistics (kStats), pack at the width the header's
+// statistics give (kPack), or statistics plus every field written at the
+// speculative width (kSpec).  kPack with `spec` set follows a kSpec launch
+// and returns after the header when the exact width is the speculative one.
+constexpr int kStats = 0, kPack = 1, kSpec = 2;
+
+template <class Op, int BMAX, int MODE>
 __global__ void __launch_bounds__(kThreads) k_ew(Op op, ccm_header* out, uint32_t* words,
-                                                 uint64_t capacity, uint64_t n) {
+                                                 uint64_t capacity, uint64_t n, int spec) {
   using V = typename Op::template Val<BMAX>;
   using U = typename std::make_unsigned<V>::type;
   constexpr int kSignShift = 8 * sizeof(V) - 1;
   __shared__ __align__(16) uint32_t s_buf[kWarps][kBufWords];
   int b = 0, sgn = 0;
-  if constexpr (PACK) {
+  if constexpr (MODE == kPack) {
     if (!resolve_output(out, words, capacity, n, b, sgn)) return;
+    op.init(n);
+    if (spec) {
+      const int bs = op.spec_width();
+      if (bs <= BMAX && words_for(n, bs) <= capacity && bs == b) return;  // already written
+    }
   } else {
     if (out->status != CCM_OK) return;
+    op.init(n);
+    if constexpr (MODE == kSpec) {
+      const int bs = op.spec_width();
+      if (bs <= BMAX && words_for(n, bs) <= capacity) b = bs;  // else statistics only
+    }
   }
-  op.init(n);
   const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
   uint32_t* buf = s_buf[warp];
-  const uint64_t dw = PACK ? data_words(n, b) : 0;
+  const uint64_t dw = b ? data_words(n, b) : 0;
   const uint32_t mask = b >= 32 ? 0xffffffffu : ((1u << b) - 1u);
   const uint64_t ntiles = (n + kTile - 1) / kTile;
   const uint64_t gwarps = (uint64_t)gridDim.x * kWarps;
@@ -195,14 +248,20 @@ __global__ void __launch_bounds__(kThreads) k_ew(Op op, ccm_header* out, uint32_
   if (tile < ntiles) op.template prefetch<BMAX>(cur, tile, lane);
   for (; tile < ntiles; tile += gwarps) {
     if (tile + gwarps < ntiles) op.template prefetch<BMAX>(nxt, tile + gwarps, lane);
-    if constexpr (!PACK) {
+    if (MODE == kStats || (MODE == kSpec && b == 0)) {
       op.template produce<BMAX>(cur, buf, lane, ovf, [&](int, V v) {
         orv |= (U)(v ^ (v >> kSignShift));
         negv |= v;
       });
     } else {
       uint32_t u[32];
-      op.template produce<BMAX>(cur, buf, lane, ovf, [&](int k, V v) { u[k] = (uint32_t)v & mask; });
+      op.template produce<BMAX>(cur, buf, lane, ovf, [&](int k, V v) {
+        u[k] = (uint32_t)v & mask;
+        if constexpr (MODE == kSpec) {
+          orv |= (U)(v ^ (v >> kSignShift));
+          negv |= v;
+        }
+      });
       encode_dispatch<BMAX>(b, u, buf, lane);
       __syncwarp();
       store_packed(buf, words, tile, b, dw, lane);
@@ -210,7 +269,7 @@ __global__ void __launch_bounds__(kThreads) k_ew(Op op, ccm_header* out, uint32_
     }
     cur = nxt;
   }
-  if constexpr (!PACK) {
+  if constexpr (MODE != kPack) {
     uint64_t o = warp_or64((uint64_t)orv);
     uint32_t neg = __reduce_or_sync(0xffffffffu, (uint32_t)(negv < 0));
     ovf = (int)__reduce_or_sync(0xffffffffu, (uint32_t)ovf);
@@ -222,77 +281,6 @@ __global__ void __launch_bounds__(kThreads) k_ew(Op op, ccm_header* out, uint32_
   }
 }
 
-// Single-pass form of add / scale (with workspace): values are produced once,
-// each 1024-field tile is packed at its own width b_loc into its workspace
-// slot (slot_words apart) and the tile statistics are merged into the output
-// header; k_repack then writes the result at the matrix width b (a 16-byte
-// copy for every tile whose b_loc is already b).
-template <class Op, int BMAX>
-__global__ void __launch_bounds__(kThreads) k_ew_local(Op op, ccm_header* out,
-                                                       uint32_t* __restrict__ slots,
-                                                       uint32_t slot_words,
-                                                       uint8_t* __restrict__ tile_width,
-                                                       uint64_t n) {
-  using V = typename Op::template Val<BMAX>;
-  using U = typename std::make_unsigned<V>::type;
-  constexpr int kSignShift = 8 * sizeof(V) - 1;
-  __shared__ __align__(16) uint32_t s_buf[kWarps][kBufWords];
-  if (out->status != CCM_OK) return;
-  op.init(n);
-  const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
-  uint32_t* buf = s_buf[warp];
-  const uint64_t ntiles = (n + kTile - 1) / kTile;
-  const uint64_t gwarps = (uint64_t)gridDim.x * kWarps;
-  uint64_t g_or = 0;
-  uint32_t g_neg = 0;
-  int ovf = 0;
-  uint64_t tile = (uint64_t)blockIdx.x * kWarps + warp;
-  typename Op::template Regs<BMAX> cur, nxt;
-  if (tile < ntiles) op.template prefetch<BMAX>(cur, tile, lane);
-  for (; tile < ntiles; tile += gwarps) {
-    if (tile + gwarps < ntiles) op.template prefetch<BMAX>(nxt, tile + gwarps, lane);
-    V val[32];
-    U orv = 0;
-    V negv = 0;
-    op.template produce<BMAX>(cur, buf, lane, ovf, [&](int k, V v) {
-      val[k] = v;
-      orv |= (U)(v ^ (v >> kSignShift));
-      negv |= v;
-    });
-    const uint64_t o = warp_or64((uint64_t)orv);
-    const uint32_t neg = __reduce_or_sync(0xffffffffu, (uint32_t)(negv < 0));
-    g_or |= o;
-    g_neg |= neg;
-    const int bl = width_from_stats(o, neg);
-    if (bl <= BMAX && bl <= 32) {
-      uint32_t u[32];
-      const uint32_t mask = bl >= 32 ? 0xffffffffu : ((1u << bl) - 1u);
-#pragma unroll
-      for (int k = 0; k < 32; ++k) u[k] = (uint32_t)val[k] & mask;
-      encode_dispatch<BMAX>(bl, u, buf, lane);
-      __syncwarp();
-      uint4* dst = reinterpret_cast<uint4*>(slots + tile * (uint64_t)slot_words);
-      if (32 * bl <= (int)slot_words) {
-        for (int q = lane; q < 8 * bl; q += 32) {
-          const int w = 4 * q;
-          dst[q] = make_uint4(buf[stage_pos(w, bl)], buf[stage_pos(w + 1, bl)],
-                              buf[stage_pos(w + 2, bl)], buf[stage_pos(w + 3, bl)]);
-        }
-      }
-      __syncwarp();
-    }
-    if (lane == 0)
-      tile_width[tile] = (bl <= BMAX && 32 * bl <= (int)slot_words) ? (uint8_t)(bl | (neg ? 0x80 : 0))
-                                                                   : 0xFF;
-    cur = nxt;
-  }
-  ovf = (int)__reduce_or_sync(0xffffffffu, (uint32_t)ovf);
-  if (lane == 0) {
-    if (g_or) atomicOr(reinterpret_cast<unsigned long long*>(&out->stat_or), (unsigned long long)g_or);
-    if (g_neg) atomicOr(&out->stat_neg, 1u);
-    if (ovf) set_status(out, CCM_E_OVERFLOW);
-  }
-}
 
 // Pack pass of a dense int32/int64 matrix (its statistics come from k_stats).
 template <typename T, int BMAX>
@@ -548,8 +536,8 @@ __global__ void __launch_bounds__(kThreads) k_unpack_ge(const ccm_header* h,
 
 // What the host asks one class to run.
 enum class EwKind {
-  PackI64, PackI32, AddStats, AddPack, ScaleStats, ScalePack, UnpackI64, UnpackI32,
-  LocalI64, LocalI32, LocalAdd, LocalScale, Repack
+  PackI64, PackI32, AddStats, AddSpec, AddPack, ScaleStats, ScaleSpec, ScalePack, UnpackI64,
+  UnpackI32, LocalI64, LocalI32, Repack
 };
 
 struct EwCall {
@@ -567,6 +555,7 @@ struct EwCall {
   int32_t* err;           // unpack status
   void* ws;               // Local* / Repack: workspace (slots, then tile widths)
   int slot_class;         // Local* / Repack: width class of the output (slot = 32*class words)
+  int spec;               // AddPack / ScalePack: an AddSpec / ScaleSpec launch came first
 };
 
 inline int ew_grid(uint64_t n, int per_sm) {
@@ -591,31 +580,46 @@ void launch_ew_class(const EwCall& c, cudaStream_t st) {
           (const int32_t*)c.dense, c.out, c.words, c.capacity, n);
       break;
     case EwKind::AddStats:
-      k_ew<OpAdd, C, false><<<g, kThreads, 0, st>>>(OpAdd{a, b}, c.out, nullptr, 0, n);
+    case EwKind::AddSpec:
+    case EwKind::AddPack: {
+      const OpAdd op{a, b};
+      if (c.kind == EwKind::AddStats)
+        k_ew<OpAdd, C, kStats><<<g, kThreads, 0, st>>>(op, c.out, nullptr, 0, n, 0);
+      else if (c.kind == EwKind::AddSpec)
+        k_ew<OpAdd, C, kSpec><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity, n, 0);
+      else
+        k_ew<OpAdd, C, kPack><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity, n, c.spec);
       break;
-    case EwKind::AddPack:
-      k_ew<OpAdd, C, true><<<g, kThreads, 0, st>>>(OpAdd{a, b}, c.out, c.words, c.capacity, n);
-      break;
+    }
     case EwKind::ScaleStats:
-      if (c.s > -32768 && c.s < 32768)
-        k_ew<OpScale<true>, C, false><<<g, kThreads, 0, st>>>(OpScale<true>{a, c.s}, c.out,
-                                                               nullptr, 0, n);
-      else
-        k_ew<OpScale<false>, C, false><<<g, kThreads, 0, st>>>(OpScale<false>{a, c.s}, c.out,
-                                                                nullptr, 0, n);
+    case EwKind::ScaleSpec:
+    case EwKind::ScalePack: {
+      const bool small = c.s > -32768 && c.s < 32768;
+      if (small) {
+        const OpScale<true> op{a, c.s};
+        if (c.kind == EwKind::ScaleStats)
+          k_ew<OpScale<true>, C, kStats><<<g, kThreads, 0, st>>>(op, c.out, nullptr, 0, n, 0);
+        else if (c.kind == EwKind::ScaleSpec)
+          k_ew<OpScale<true>, C, kSpec><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity,
+                                                                n, 0);
+        else
+          k_ew<OpScale<true>, C, kPack><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity,
+                                                                n, c.spec);
+      } else {
+        const OpScale<false> op{a, c.s};
+        if (c.kind == EwKind::ScaleStats)
+          k_ew<OpScale<false>, C, kStats><<<g, kThreads, 0, st>>>(op, c.out, nullptr, 0, n, 0);
+        else if (c.kind == EwKind::ScaleSpec)
+          k_ew<OpScale<false>, C, kSpec><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity,
+                                                                 n, 0);
+        else
+          k_ew<OpScale<false>, C, kPack><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity,
+                                                                 n, c.spec);
+      }
       break;
-    case EwKind::ScalePack:
-      if (c.s > -32768 && c.s < 32768)
-        k_ew<OpScale<true>, C, true><<<g, kThreads, 0, st>>>(OpScale<true>{a, c.s}, c.out,
-                                                              c.words, c.capacity, n);
-      else
-        k_ew<OpScale<false>, C, true><<<g, kThreads, 0, st>>>(OpScale<false>{a, c.s}, c.out,
-                                                               c.words, c.capacity, n);
-      break;
+    }
     case EwKind::LocalI64:
     case EwKind::LocalI32:
-    case EwKind::LocalAdd:
-    case EwKind::LocalScale:
     case EwKind::Repack: {
       const uint64_t ntiles = (n + kTile - 1) / kTile;
       const int sc = c.slot_class;
@@ -637,20 +641,10 @@ void launch_ew_class(const EwCall& c, cudaStream_t st) {
         const size_t smem = (size_t)kWarps * kBufWords * sizeof(uint32_t);
         k_pack_local<int32_t, C><<<gl, kThreads, smem, st>>>((const int32_t*)c.dense, c.out,
                                                              slots, slot_words, widths, n);
-      }
-      else if (c.kind == EwKind::LocalAdd)
-        k_ew_local<OpAdd, C><<<g, kThreads, 0, st>>>(OpAdd{a, b}, c.out, slots, slot_words,
-                                                     widths, n);
-      else if (c.kind == EwKind::LocalScale) {
-        if (c.s > -32768 && c.s < 32768)
-          k_ew_local<OpScale<true>, C><<<g, kThreads, 0, st>>>(OpScale<true>{a, c.s}, c.out, slots,
-                                                                slot_words, widths, n);
-        else
-          k_ew_local<OpScale<false>, C><<<g, kThreads, 0, st>>>(OpScale<false>{a, c.s}, c.out,
-                                                                 slots, slot_words, widths, n);
-      } else
+      } else {
         k_repack<C><<<gl, kThreads, 0, st>>>(slots, slot_words, widths, c.out, c.words, c.capacity,
                                              n);
+      }
       break;
     }
     case EwKind::UnpackI64:

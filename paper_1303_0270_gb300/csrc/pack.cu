@@ -293,8 +293,8 @@ void run_get(const ccm_matrix& a, const uint64_t* idx, uint64_t count, int64_t* 
 // ---------------------------------------------------------------------------
 // add / scale
 // ---------------------------------------------------------------------------
-void run_add(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, void* ws,
-             size_t ws_bytes, cudaStream_t st) {
+void run_add(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, void* /*ws*/,
+             size_t /*ws_bytes*/, cudaStream_t st) {
   InitArgs ia{};
   ia.out = c.hdr;
   ia.in0 = a.hdr;
@@ -311,29 +311,6 @@ void run_add(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, void
   uint64_t n = c.rows * c.cols;
   const int cls = ew_class(max(max(width_bound(a.capacity, n), width_bound(b.capacity, n)),
                                width_bound(c.capacity, n)));
-  const int out_cls = ew_class(width_bound(c.capacity, n));
-  if (cls && n && out_cls && ws && ws_bytes >= ge::pack_ws_bytes(n, out_cls)) {
-    // one pass over the inputs: tiles at their own width, then re-coded
-    ge::EwCall e{};
-    e.ha = a.hdr;
-    e.wa = a.words;
-    e.hb = b.hdr;
-    e.wb = b.words;
-    e.out = c.hdr;
-    e.words = c.words;
-    e.capacity = c.capacity;
-    e.rows = c.rows;
-    e.cols = c.cols;
-    e.ws = ws;
-    e.slot_class = out_cls;
-    e.kind = ge::EwKind::LocalAdd;
-    profile_begin(st);
-    launch_ew(cls, e, st);
-    profile_end(st);
-    e.kind = ge::EwKind::Repack;
-    launch_ew(cls, e, st);
-    return;
-  }
   if (cls && n) {
     ge::EwCall e{};
     e.ha = a.hdr;
@@ -345,10 +322,13 @@ void run_add(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, void
     e.capacity = c.capacity;
     e.rows = c.rows;
     e.cols = c.cols;
-    e.kind = ge::EwKind::AddStats;
+    // one pass at the width the input ranges give, then the finish (a second
+    // pass only when the exact width is smaller)
+    e.kind = ge::EwKind::AddSpec;
+    profile_begin(st);
     launch_ew(cls, e, st);
     e.kind = ge::EwKind::AddPack;
-    profile_begin(st);
+    e.spec = 1;
     launch_ew(cls, e, st);
     profile_end(st);
     return;
@@ -360,8 +340,8 @@ void run_add(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, void
   profile_end(st);
 }
 
-void run_scale(const ccm_matrix& a, int64_t s, const ccm_matrix& c, void* ws, size_t ws_bytes,
-               cudaStream_t st) {
+void run_scale(const ccm_matrix& a, int64_t s, const ccm_matrix& c, void* /*ws*/,
+               size_t /*ws_bytes*/, cudaStream_t st) {
   InitArgs ia{};
   ia.out = c.hdr;
   ia.in0 = a.hdr;
@@ -373,27 +353,6 @@ void run_scale(const ccm_matrix& a, int64_t s, const ccm_matrix& c, void* ws, si
   launch_init(ia, st);
   uint64_t n = c.rows * c.cols;
   const int cls = ew_class(max(width_bound(a.capacity, n), width_bound(c.capacity, n)));
-  const int out_cls = ew_class(width_bound(c.capacity, n));
-  if (cls && n && out_cls && ws && ws_bytes >= ge::pack_ws_bytes(n, out_cls)) {
-    ge::EwCall e{};
-    e.ha = a.hdr;
-    e.wa = a.words;
-    e.s = s;
-    e.out = c.hdr;
-    e.words = c.words;
-    e.capacity = c.capacity;
-    e.rows = c.rows;
-    e.cols = c.cols;
-    e.ws = ws;
-    e.slot_class = out_cls;
-    e.kind = ge::EwKind::LocalScale;
-    profile_begin(st);
-    launch_ew(cls, e, st);
-    profile_end(st);
-    e.kind = ge::EwKind::Repack;
-    launch_ew(cls, e, st);
-    return;
-  }
   if (cls && n) {
     ge::EwCall e{};
     e.ha = a.hdr;
@@ -404,10 +363,11 @@ void run_scale(const ccm_matrix& a, int64_t s, const ccm_matrix& c, void* ws, si
     e.capacity = c.capacity;
     e.rows = c.rows;
     e.cols = c.cols;
-    e.kind = ge::EwKind::ScaleStats;
+    e.kind = ge::EwKind::ScaleSpec;
+    profile_begin(st);
     launch_ew(cls, e, st);
     e.kind = ge::EwKind::ScalePack;
-    profile_begin(st);
+    e.spec = 1;
     launch_ew(cls, e, st);
     profile_end(st);
     return;

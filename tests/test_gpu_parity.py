@@ -266,19 +266,64 @@ def test_width_class_and_runtime_kernels_agree(ccm, b):
     assert_same_packed(pa_rt, oa, f"runtime pack b={b}")
     assert np.array_equal(ccm.unpack(pa_fast).cpu().numpy(), a)
     assert np.array_equal(ccm.unpack(pa_fast, dtype=torch.int32).cpu().numpy(), a)
+    # output capacities: the exact width (the speculative width may not fit:
+    # statistics then pack), a few bits more, and 64 bits (the run-time kernels)
     s_exp = oracle.add(oa, oc)
     for cap in (s_exp.width, s_exp.width + 3, 64):
-        for single in (True, False):
-            out = ccm.PackedMatrix(*shape, ccm.words_for(*shape, cap), device())
-            assert_same_packed(ccm.add_into(pa_fast, pc_fast, out, single_pass=single), s_exp,
-                               f"add b={b} cap={cap} single={single}")
+        out = ccm.PackedMatrix(*shape, ccm.words_for(*shape, cap), device())
+        assert_same_packed(ccm.add_into(pa_fast, pc_fast, out), s_exp, f"add b={b} cap={cap}")
     for s in (-3, 1 << 20):
         d_exp = oracle.scale(oa, s)
         for cap in (d_exp.width, 64):
-            for single in (True, False):
-                out = ccm.PackedMatrix(*shape, ccm.words_for(*shape, cap), device())
-                assert_same_packed(ccm.scale_into(pa_fast, s, out, single_pass=single), d_exp,
-                                   f"scale {s} b={b} cap={cap} single={single}")
+            out = ccm.PackedMatrix(*shape, ccm.words_for(*shape, cap), device())
+            assert_same_packed(ccm.scale_into(pa_fast, s, out), d_exp,
+                               f"scale {s} b={b} cap={cap}")
+
+
+@pytest.mark.parametrize("ba,sa,bb,sb", [(5, 0, 5, 0), (7, 1, 3, 0), (3, 0, 7, 1), (8, 1, 8, 1),
+                                         (16, 1, 1, 0), (13, 0, 13, 0), (31, 1, 31, 1)])
+@pytest.mark.parametrize("hit", [True, False])
+def test_add_speculative_width(ccm, ba, sa, bb, sb, hit):
+    """The one-pass add writes C at the width the input ranges bound the sum
+    to; that bound is reached (hit: entries at the range extremes, one pass)
+    or not (miss: extremes avoided, the exact width is smaller and the second
+    pass re-packs).  Both against the oracle word for word."""
+    shape = (9, 3001)
+    a = _rand(ba * 7 + sa, shape, ba, bool(sa))
+    b = _rand(bb * 11 + sb, shape, bb, bool(sb))
+    lo_a, hi_a = synth.signed_range(ba) if sa else (0, (1 << ba) - 1)
+    lo_b, hi_b = synth.signed_range(bb) if sb else (0, (1 << bb) - 1)
+    if hit:  # one pair at the top of both ranges and one at the bottom
+        a.flat[5], b.flat[5], a.flat[9], b.flat[9] = hi_a, hi_b, lo_a, lo_b
+    else:    # a still needs ba bits and b bb bits, but no extreme meets another
+        a[:] = np.clip(a, lo_a // 2, hi_a // 2)
+        b[:] = np.clip(b, lo_b // 2, hi_b // 2)
+        a.flat[0], b.flat[0], a.flat[1], b.flat[1] = hi_a, 0, 0, hi_b
+        a.flat[2], b.flat[2], a.flat[3], b.flat[3] = lo_a, 0, 0, lo_b
+    oa, ob = oracle.pack(a), oracle.pack(b)
+    assert (oa.width, ob.width) == (ba, bb)
+    expect = oracle.add(oa, ob)
+    got = ccm.add(ccm.pack(to_dev(a)), ccm.pack(to_dev(b)))
+    assert_same_packed(got, expect, f"add spec {ba}/{sa} + {bb}/{sb} hit={hit}")
+
+
+@pytest.mark.parametrize("b,sgn", [(5, 0), (4, 1), (12, 1), (20, 0)])
+@pytest.mark.parametrize("s", [7, -7, 8, 1, 0, -1, 3000, -40000])
+def test_scale_speculative_width(ccm, b, sgn, s):
+    """One-pass scale: s times the range of A's width; the maximum entry at the
+    range top (hit) and below it (the exact width may be smaller: second pass)."""
+    shape = (7, 2049)
+    a = _rand(b * 3 + sgn, shape, b, bool(sgn))
+    for top in (True, False):
+        lo, hi = synth.signed_range(b) if sgn else (0, (1 << b) - 1)
+        v = a.copy()
+        if not top:
+            v = np.clip(v, lo // 2 if sgn else 0, (hi // 2) + 1)
+            v.flat[0] = (hi // 2) + 1
+        oa = oracle.pack(v)
+        expect = oracle.scale(oa, s)
+        assert_same_packed(ccm.scale(ccm.pack(to_dev(v)), s), expect,
+                           f"scale spec b={b} s={sgn} by {s} top={top}")
 
 
 @pytest.mark.parametrize("m,n", [(1, 128), (31, 256), (300, 384), (257, 1280), (1000, 128)])
