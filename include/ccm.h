@@ -193,6 +193,18 @@ ccm_status ccm_scale(const ccm_matrix* a, int64_t s, const ccm_matrix* c, void* 
 ccm_status ccm_matvec(const ccm_matrix* a, const ccm_matrix* x, const ccm_matrix* y, void* ws,
                       size_t ws_bytes, ccm_stream_t stream);
 
+/* y = A x + B z in one chain that stays compressed: A is m x n1, B is
+ * m x n2, x and z packed n1 x 1 and n2 x 1; both products are summed exactly
+ * in one int64 scratch and y is packed once, at the sum's exact width (no
+ * intermediate vector is packed or unpacked).  The paper's setting of
+ * producing, compressing and then manipulating data (Introduction) as one
+ * operation; CCM_E_OVERFLOW when y_i does not fit int64.  `ws`: at least
+ * ccm_workspace_bytes(CCM_OP_MATVEC, m, max(n1, n2), 1) bytes, 256-byte
+ * aligned. */
+ccm_status ccm_matvec2(const ccm_matrix* a, const ccm_matrix* x, const ccm_matrix* b,
+                       const ccm_matrix* z, const ccm_matrix* y, void* ws, size_t ws_bytes,
+                       ccm_stream_t stream);
+
 /* C = A B: A is m x k, B is k x n, C is m x n, exact int64 entries
  * (CCM_E_OVERFLOW otherwise), re-packed at C's own width.  `path` selects the
  * tensor-core limb path or the CUDA-core path (AUTO = tensor when the inputs

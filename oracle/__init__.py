@@ -243,6 +243,21 @@ def matmul(pa: Packed, pb: Packed) -> Packed:
     return pack(matmul_dense(unpack(pa), unpack(pb)))
 
 
+# Chains that stay compressed: the same integers as the chain on the
+# uncompressed operands (Introduction), re-packed once at the end.
+def matvec2(pa: Packed, px: Packed, pb: Packed, pz: Packed) -> Packed:
+    """y = A x + B z (int64 overflow of the sum raises, as in add_dense)."""
+    assert pa.rows == pb.rows and px.n == pa.cols and pz.n == pb.cols
+    ya = matvec_dense(unpack(pa), unpack(px).ravel())
+    yb = matvec_dense(unpack(pb), unpack(pz).ravel())
+    return pack(add_dense(ya, yb).reshape(pa.rows, 1))
+
+
+def matvec_chain(pa: Packed, pb: Packed, px: Packed) -> Packed:
+    """y = A (B x), the intermediate B x packed at its own width."""
+    return matvec(pa, matvec(pb, px))
+
+
 # VLB, Method 2: a k-bit length prefix then the entry in its own bit length.
 @dataclass
 class Vlb:

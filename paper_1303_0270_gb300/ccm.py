@@ -89,6 +89,7 @@ SIGNATURES = {
     "ccm_vlb_index_entries": ([_u64, _u64], _u64),
     "ccm_vlb_pack": ([_vp, _i32, _u64, _u64, _vp, _vp, _u64, _vp, _vp, _sz, _vp], _i32),
     "ccm_vlb_unpack": ([_vp, _vp, _u64, _vp, _u64, _u64, _vp, _i32, _vp, _vp], _i32),
+    "ccm_matvec2": ([_MP, _MP, _MP, _MP, _MP, _vp, _sz, _vp], _i32),
     "ccm_vlb_matvec": ([_vp, _vp, _u64, _vp, _u64, _u64, _MP, _MP, _vp, _sz, _vp], _i32),
     "ccm_launch_count": ([], _u64),
     "ccm_profile_next": ([_vp, _vp], _i32),
@@ -359,6 +360,33 @@ def matvec(a: PackedMatrix, x: PackedMatrix, capacity: int | None = None, stream
         capacity = _bound_capacity(a.rows, 1, a.width_bound() + x.width_bound() +
                                    _bitlen(a.cols) + 1)
     return matvec_into(a, x, PackedMatrix(a.rows, 1, capacity, a.device), stream=stream)
+
+
+def matvec2_into(a: PackedMatrix, x: PackedMatrix, b: PackedMatrix, z: PackedMatrix,
+                 y: PackedMatrix, ws: torch.Tensor | None = None, stream=None) -> PackedMatrix:
+    """y = A x + B z, both products summed before y is packed once."""
+    if ws is None:
+        ws = workspace(OP_MATVEC, a.rows, max(a.cols, b.cols), 1, a.device)
+    ma, mx, mb, mz, my = a.c(), x.c(), b.c(), z.c(), y.c()
+    _check(lib().ccm_matvec2(ctypes.byref(ma), ctypes.byref(mx), ctypes.byref(mb),
+                             ctypes.byref(mz), ctypes.byref(my), ctypes.c_void_p(ws.data_ptr()),
+                             ws.numel(), _stream(stream)), "ccm_matvec2")
+    y._written()
+    return y
+
+
+def matvec2(a: PackedMatrix, x: PackedMatrix, b: PackedMatrix, z: PackedMatrix,
+            capacity: int | None = None, stream=None) -> PackedMatrix:
+    if capacity is None:
+        capacity = words_for(a.rows, 1, 64)
+    return matvec2_into(a, x, b, z, PackedMatrix(a.rows, 1, capacity, a.device), stream=stream)
+
+
+def matvec_chain(a: PackedMatrix, b: PackedMatrix, x: PackedMatrix, stream=None) -> PackedMatrix:
+    """y = A (B x): the intermediate t = B x stays on the GPU, packed at its
+    own exact width, and is the x of the second product (no host round trip)."""
+    t = matvec(b, x, stream=stream)
+    return matvec(a, t, stream=stream)
 
 
 def matmul_into(a: PackedMatrix, b: PackedMatrix, c: PackedMatrix, path: int = MATMUL_AUTO,

@@ -142,6 +142,21 @@ ccm_status ccm_matvec(const ccm_matrix* a, const ccm_matrix* x, const ccm_matrix
   return launched();
 }
 
+ccm_status ccm_matvec2(const ccm_matrix* a, const ccm_matrix* x, const ccm_matrix* b,
+                       const ccm_matrix* z, const ccm_matrix* y, void* ws, size_t ws_bytes,
+                       ccm_stream_t stream) {
+  if (!valid_in(a) || !valid_in(x) || !valid_in(b) || !valid_in(z) || !valid_out(y) || !ws)
+    return CCM_E_INVAL;
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return CCM_E_INVAL;
+  if (x->rows != a->cols || x->cols != 1 || z->rows != b->cols || z->cols != 1 ||
+      b->rows != a->rows || y->rows != a->rows || y->cols != 1)
+    return CCM_E_SHAPE;
+  if (!capacity_ok(y)) return CCM_E_CAPACITY;
+  if (ws_bytes < ccm::matvec2_workspace(a->rows, a->cols, b->cols)) return CCM_E_CAPACITY;
+  ccm::run_matvec2(*a, *x, *b, *z, *y, ws, to_cuda(stream));
+  return launched();
+}
+
 ccm_status ccm_matmul(const ccm_matrix* a, const ccm_matrix* b, const ccm_matrix* c, int path,
                       void* ws, size_t ws_bytes, ccm_stream_t stream) {
   if (!valid_in(a) || !valid_in(b) || !valid_out(c) || !ws) return CCM_E_INVAL;

@@ -39,6 +39,9 @@ void run_pack_scratch(const int64_t* vals, const ccm_matrix& out, cudaStream_t s
                       bool stats_done = false);
 
 size_t matvec_workspace(uint64_t m, uint64_t n);
+size_t matvec2_workspace(uint64_t m, uint64_t n1, uint64_t n2);
+void run_matvec2(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& b,
+                 const ccm_matrix& z, const ccm_matrix& y, void* ws, cudaStream_t st);
 void run_matvec(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& y, void* ws,
                 cudaStream_t st);
 

@@ -69,11 +69,16 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec_rows(ccm_header* out, con
   for (uint64_t i = (uint64_t)blockIdx.x * (kMvThreads / kWarp) + threadIdx.x / kWarp; i < m;
        i += warps) {
     const uint64_t row0 = i * n;
+    // (added to y: a second product term may already be there)
     if (!wide) {
       int64_t acc = 0;
       for (uint64_t j = lane; j < n; j += kWarp) acc += decode_field(wa, row0 + j, ba, sa) * xs[j];
       for (int d = 16; d; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
-      if (lane == 0) y[i] = acc;
+      if (lane == 0) {
+        const __int128 t = (__int128)y[i] + acc;
+        if (!fits64(t)) ovf = 1;
+        y[i] = (int64_t)t;
+      }
     } else {
       __int128 acc = 0;
       for (uint64_t j = lane; j < n; j += kWarp)
@@ -81,7 +86,9 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec_rows(ccm_header* out, con
       for (int d = 16; d; d >>= 1) acc += shfl_down_i128(acc, d);
       if (lane == 0) {
         if (!fits64(acc)) ovf = 1;
-        y[i] = (int64_t)acc;
+        const __int128 t = (__int128)y[i] + (int64_t)acc;
+        if (!fits64(t)) ovf = 1;
+        y[i] = (int64_t)t;
       }
     }
   }
@@ -158,33 +165,22 @@ size_t matvec_workspace(uint64_t m, uint64_t n) {
   return up(n * sizeof(int64_t)) + up(m * sizeof(int64_t)) + 256;
 }
 
-void run_matvec(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& y, void* ws,
-                cudaStream_t st) {
+namespace {
+
+// Launches the kernels of one product term A x, adding it to the int64 y
+// scratch `yv` (zeroed by the caller).  `budget`: the bit bound every partial
+// sum of this term must stay under for the int64 streaming kernels (63 for
+// one term, 62 when two terms are summed).  `xs`: the x region of the
+// workspace (8n bytes).
+void matvec_term(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& y, int64_t* xs,
+                 int64_t* yv, int budget, cudaStream_t st) {
   const uint64_t m = a.rows, n = a.cols;
-  auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
-  int64_t* xs = (int64_t*)ws;
-  int64_t* yv = (int64_t*)((char*)ws + up(n * sizeof(int64_t)));
-  InitArgs ia{};
-  ia.out = y.hdr;
-  ia.in0 = a.hdr;
-  ia.in0_rows = a.rows;
-  ia.in0_cols = a.cols;
-  ia.in0_capacity = a.capacity;
-  ia.in1 = x.hdr;
-  ia.in1_rows = x.rows;
-  ia.in1_cols = x.cols;
-  ia.in1_capacity = x.capacity;
-  ia.out_rows = y.rows;
-  ia.out_cols = y.cols;
-  if (n == 0) {  // an empty inner dimension gives y = 0
-    ia.zero_ptr = yv;
-    ia.zero_count = m;
-  }
+  if (!m || !n) return;  // an empty inner dimension adds 0
   const int bmax_a = width_bound(a.capacity, m * n), bmax_x = width_bound(x.capacity, n);
   // Streaming kernels: row-aligned A (cols % 128 == 0), fields of at most 32
-  // bits, x of at most 31, and every partial sum inside int64.
-  const bool aligned = m && n && n % mvf::kKC == 0 && bmax_a <= 32 && bmax_x <= 31 &&
-                       bmax_a + bmax_x + bitlen_host(n) <= 63;
+  // bits, x of at most 31, and every partial sum inside the budget.
+  const bool aligned = n % mvf::kKC == 0 && bmax_a <= 32 && bmax_x <= 31 &&
+                       bmax_a + bmax_x + bitlen_host(n) <= budget;
   const bool narrow = bmax_a + bmax_x + 7 <= 31;
   // Row-streaming kernel when all of x fits in shared memory beside the
   // rings: CTAs of 8 or 4 warps, whichever keeps more warps resident.
@@ -217,13 +213,25 @@ void run_matvec(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& y, v
       }
     }
   }
-  const bool use_rows = rplan.warps > 0;
-  // (the slab kernel addresses a warp's 32 rows with 32-bit offsets)
-  bool fast = !use_rows && aligned && n * (uint64_t)bmax_a < (1ull << 30);
-  // Launch plan for CTAs of `warps` warps: one wave of as many CTAs as stay
-  // resident; column slabs split the work when there are fewer row blocks
-  // than that, CTAs loop over row blocks when there are more.  A slab's x
-  // (int32) must fit in shared memory beside the stage rings.
+  if (rplan.warps > 0) {
+    uint8_t* img = reinterpret_cast<uint8_t*>(xs);  // n * 8 bytes >= the image
+    const unsigned gx = (unsigned)umin(n / mvf::kKC, (uint64_t)num_sms() * 8);
+    mvf::rows::k_xprep<<<gx, mvf::kKC, 0, st>>>(y.hdr, a.hdr, x.hdr, x.words, n, img);
+    note_launch();
+    mvf::rows::RowArgs ra{y.hdr, a.hdr, a.words, x.hdr, x.words, m, n, 0u, 0u, yv, img};
+    ra.warp_region = mvf::warp_region_bytes(bmax_a);
+    ra.x_offset = (uint32_t)((size_t)rplan.warps * ra.warp_region);
+    profile_begin(st);
+    mvf::rows::launch(bmax_a, ra, narrow, rplan.grid, rplan.warps * 32, rplan.smem, st);
+    profile_end(st);
+    note_launch();
+    return;
+  }
+  // Column-slab kernel (the slab kernel addresses a warp's 32 rows with
+  // 32-bit offsets).  Launch plan for CTAs of `warps` warps: one wave of as
+  // many CTAs as stay resident; column slabs split the work when there are
+  // fewer row blocks than that, CTAs loop over row blocks when there are
+  // more.  A slab's x (int32) must fit in shared memory beside the rings.
   struct Plan {
     int warps;
     uint64_t grid_x, splits, per, resident_warps;
@@ -252,62 +260,84 @@ void run_matvec(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& y, v
     p.resident_warps = umin(p.grid_x * p.splits, resident) * warps;
     return p;
   };
-  Plan plan{};
-  if (fast) {
-    plan = make_plan(8);
+  if (aligned && n * (uint64_t)bmax_a < (1ull << 30)) {
+    Plan plan = make_plan(8);
     const Plan p4 = make_plan(4);
     if (p4.resident_warps > plan.resident_warps) plan = p4;
-    fast = plan.per > 0;
+    if (plan.per > 0) {
+      const int warps = plan.warps;
+      mvf::Args args{y.hdr, a.hdr, a.words, x.hdr, x.words, m, n,
+                     (uint32_t)(plan.per * mvf::kKC), 0u, 0u, yv};
+      args.stage_region = (uint32_t)((size_t)warps * warp_region);
+      args.warp_region = warp_region;
+      dim3 grid((unsigned)plan.grid_x, (unsigned)plan.splits);
+      profile_begin(st);
+      if (bmax_a <= 8)
+        mvf::launch_matvec_fast8(args, narrow, grid, warps * 32, plan.smem, st);
+      else if (bmax_a <= 16)
+        mvf::launch_matvec_fast16(args, narrow, grid, warps * 32, plan.smem, st);
+      else
+        mvf::launch_matvec_fast32(args, narrow, grid, warps * 32, plan.smem, st);
+      profile_end(st);
+      note_launch();
+      return;
+    }
   }
-  if (fast || use_rows) ia.zero_ptr = yv, ia.zero_count = m;
-  launch_init(ia, st);
-  if (use_rows) {
-    uint8_t* img = reinterpret_cast<uint8_t*>(xs);  // n * 8 bytes >= the image
-    const unsigned gx = (unsigned)umin(n / mvf::kKC, (uint64_t)num_sms() * 8);
-    mvf::rows::k_xprep<<<gx, mvf::kKC, 0, st>>>(y.hdr, a.hdr, x.hdr, x.words, n, img);
-    note_launch();
-    mvf::rows::RowArgs ra{y.hdr, a.hdr, a.words, x.hdr, x.words, m, n, 0u, 0u, yv, img};
-    ra.warp_region = mvf::warp_region_bytes(bmax_a);
-    ra.x_offset = (uint32_t)((size_t)rplan.warps * ra.warp_region);
-    profile_begin(st);
-    mvf::rows::launch(bmax_a, ra, narrow, rplan.grid, rplan.warps * 32, rplan.smem, st);
-    profile_end(st);
-    note_launch();
-    run_pack_scratch(yv, y, st);
-    return;
-  }
-  if (fast) {
-    const int warps = plan.warps;
-    mvf::Args args{y.hdr, a.hdr, a.words, x.hdr, x.words, m, n,
-                   (uint32_t)(plan.per * mvf::kKC), 0u, 0u, yv};
-    args.stage_region = (uint32_t)((size_t)warps * warp_region);
-    args.warp_region = warp_region;
-    const size_t smem = plan.smem;
-    dim3 grid((unsigned)plan.grid_x, (unsigned)plan.splits);
-    profile_begin(st);
-    if (bmax_a <= 8)
-      mvf::launch_matvec_fast8(args, narrow, grid, warps * 32, smem, st);
-    else if (bmax_a <= 16)
-      mvf::launch_matvec_fast16(args, narrow, grid, warps * 32, smem, st);
-    else
-      mvf::launch_matvec_fast32(args, narrow, grid, warps * 32, smem, st);
-    profile_end(st);
-    note_launch();
-    run_pack_scratch(yv, y, st);
-    return;
-  }
-  if (n) {
-    int g = (int)umin((n + 255) / 256, (uint64_t)num_sms() * 4);
-    k_decode_vec<<<g, 256, 0, st>>>(y.hdr, x.hdr, x.words, n, xs);
-    note_launch();
-  }
-  if (m && n) {
-    int g = (int)umin((m + 7) / 8, (uint64_t)num_sms() * 8);
-    profile_begin(st);
-    k_matvec_rows<<<g, kMvThreads, 0, st>>>(y.hdr, a.hdr, a.words, x.hdr, xs, m, n, yv);
-    profile_end(st);
-    note_launch();
-  }
+  // generic: x decoded to int64, one warp per row, 128-bit sums when needed
+  int g = (int)umin((n + 255) / 256, (uint64_t)num_sms() * 4);
+  k_decode_vec<<<g, 256, 0, st>>>(y.hdr, x.hdr, x.words, n, xs);
+  note_launch();
+  g = (int)umin((m + 7) / 8, (uint64_t)num_sms() * 8);
+  profile_begin(st);
+  k_matvec_rows<<<g, kMvThreads, 0, st>>>(y.hdr, a.hdr, a.words, x.hdr, xs, m, n, yv);
+  profile_end(st);
+  note_launch();
+}
+
+InitArgs matvec_init(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& y, int64_t* yv) {
+  InitArgs ia{};
+  ia.out = y.hdr;
+  ia.in0 = a.hdr;
+  ia.in0_rows = a.rows;
+  ia.in0_cols = a.cols;
+  ia.in0_capacity = a.capacity;
+  ia.in1 = x.hdr;
+  ia.in1_rows = x.rows;
+  ia.in1_cols = x.cols;
+  ia.in1_capacity = x.capacity;
+  ia.out_rows = y.rows;
+  ia.out_cols = y.cols;
+  ia.zero_ptr = yv;
+  ia.zero_count = y.rows;
+  return ia;
+}
+
+}  // namespace
+
+void run_matvec(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& y, void* ws,
+                cudaStream_t st) {
+  auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  int64_t* xs = (int64_t*)ws;
+  int64_t* yv = (int64_t*)((char*)ws + up(a.cols * sizeof(int64_t)));
+  launch_init(matvec_init(a, x, y, yv), st);
+  matvec_term(a, x, y, xs, yv, 63, st);
+  run_pack_scratch(yv, y, st);
+}
+
+size_t matvec2_workspace(uint64_t m, uint64_t n1, uint64_t n2) {
+  return matvec_workspace(m, umax(n1, n2));
+}
+
+void run_matvec2(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& b,
+                 const ccm_matrix& z, const ccm_matrix& y, void* ws, cudaStream_t st) {
+  auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  int64_t* xs = (int64_t*)ws;
+  int64_t* yv = (int64_t*)((char*)ws + up(umax(a.cols, b.cols) * sizeof(int64_t)));
+  launch_init(matvec_init(a, x, y, yv), st);
+  launch_check(b, z, y.hdr, st);
+  // both products summed into one int64 scratch, each kept below 2^62
+  matvec_term(a, x, y, xs, yv, 62, st);
+  matvec_term(b, z, y, xs, yv, 62, st);
   run_pack_scratch(yv, y, st);
 }
 

@@ -91,6 +91,32 @@ __global__ void k_init(InitArgs a) {
   }
 }
 
+// Validates one more pair of inputs against an already initialised output:
+// the first invalid header's status goes to the output header.
+__global__ void k_check(InitArgs a) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int st = CCM_OK;
+    if (a.in0) st = check_input(a.in0, a.in0_rows, a.in0_cols, a.in0_capacity);
+    if (st == CCM_OK && a.in1) st = check_input(a.in1, a.in1_rows, a.in1_cols, a.in1_capacity);
+    if (st != CCM_OK) set_status(a.out, st);
+  }
+}
+
+void launch_check(const ccm_matrix& p, const ccm_matrix& q, ccm_header* out, cudaStream_t st) {
+  InitArgs ia{};
+  ia.out = out;
+  ia.in0 = p.hdr;
+  ia.in0_rows = p.rows;
+  ia.in0_cols = p.cols;
+  ia.in0_capacity = p.capacity;
+  ia.in1 = q.hdr;
+  ia.in1_rows = q.rows;
+  ia.in1_cols = q.cols;
+  ia.in1_capacity = q.capacity;
+  k_check<<<1, 32, 0, st>>>(ia);
+  note_launch();
+}
+
 void launch_init(const InitArgs& a, cudaStream_t st) {
   int grid = 1;
   if (a.zero_ptr && a.zero_count > 256)

@@ -239,5 +239,6 @@ void launch_pack(const P& prod, ccm_header* out, uint32_t* words, uint64_t capac
 }
 
 void launch_init(const InitArgs& a, cudaStream_t st);
+void launch_check(const ccm_matrix& p, const ccm_matrix& q, ccm_header* out, cudaStream_t st);
 
 }  // namespace ccm

@@ -142,3 +142,38 @@ def test_get_flat_matches_unpack():
     p = oracle.pack(a)
     idx = [0, 53, 17, 8, 9]
     assert oracle.get_flat(p, idx).tolist() == [int(a.ravel()[e]) for e in idx]
+
+
+@pytest.mark.parametrize("m,n1,n2", [(1, 1, 1), (3, 5, 2), (7, 4, 9), (5, 0, 3)])
+def test_matvec2_textbook(m, n1, n2):
+    """y_i = sum_j a_ij x_j + sum_j b_ij z_j with Python integers."""
+    rng = np.random.default_rng(m * 100 + n1 * 10 + n2)
+    a, b = _rand(rng, (m, n1), 9), _rand(rng, (m, n2), 13)
+    x, z = _rand(rng, (n1, 1), 7), _rand(rng, (n2, 1), 5)
+    want = [sum(int(a[i, j]) * int(x[j, 0]) for j in range(n1)) +
+            sum(int(b[i, j]) * int(z[j, 0]) for j in range(n2)) for i in range(m)]
+    got = oracle.matvec2(oracle.pack(a, m, n1), oracle.pack(x, n1, 1), oracle.pack(b, m, n2),
+                         oracle.pack(z, n2, 1))
+    _expect_packed(got, np.array(want).reshape(m, 1))
+
+
+def test_matvec2_overflow_of_the_sum():
+    """Each product fits int64, their sum does not."""
+    a = np.array([[1 << 62]], dtype=np.int64)
+    x = np.array([[1]], dtype=np.int64)
+    with pytest.raises(OverflowError):
+        oracle.matvec2(oracle.pack(a), oracle.pack(x), oracle.pack(a), oracle.pack(x))
+    neg = oracle.matvec2(oracle.pack(a), oracle.pack(x), oracle.pack(-a), oracle.pack(x))
+    _expect_packed(neg, np.zeros((1, 1), dtype=np.int64))
+
+
+def test_matvec_chain_associates():
+    """A (B x) == (A B) x exactly, and both equal the textbook loops."""
+    rng = np.random.default_rng(11)
+    a, b, x = _rand(rng, (4, 6), 8), _rand(rng, (6, 3), 8), _rand(rng, (3, 1), 8)
+    want = np.array(_py_matmul(a, np.array(_py_matmul(b, x), dtype=object)), dtype=object)
+    chain = oracle.matvec_chain(oracle.pack(a), oracle.pack(b), oracle.pack(x))
+    _expect_packed(chain, want)
+    ab_x = oracle.matvec(oracle.matmul(oracle.pack(a), oracle.pack(b)), oracle.pack(x))
+    assert (ab_x.width, ab_x.is_signed) == (chain.width, chain.is_signed)
+    assert np.array_equal(ab_x.words, chain.words)
