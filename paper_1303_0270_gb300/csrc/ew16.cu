@@ -5,7 +5,7 @@
 namespace ccm {
 namespace ge {
 
-template void launch_ew_class<16>(const EwCall& c, cudaStream_t st);
+template int launch_ew_class<16>(const EwCall& c, cudaStream_t st);
 
 }  // namespace ge
 }  // namespace ccm

@@ -107,6 +107,81 @@ __device__ __forceinline__ int range_width(int64_t lo, int64_t hi) {
   return 1 + (h > l ? h : l);
 }
 
+// Byte lanes: four fields of at most 8 bits in one 32-bit register, field k
+// in byte k.  spread_c<B> moves four consecutive B-bit fields there,
+// compact_c<C> moves byte k back to bits [k C, (k + 1) C); both in two
+// steps (pairs of fields into 16-bit halves, then fields into bytes) with
+// shifts and masks fixed at compile time.
+template <int B>
+__device__ __forceinline__ uint32_t spread_c(const uint32_t* w, int c) {
+  const int bit = 4 * B * c, wi = bit >> 5, sh = bit & 31;
+  const uint32_t x = sh + 4 * B <= 32 ? (w[wi] >> sh) : __funnelshift_r(w[wi], w[wi + 1], sh);
+  constexpr uint32_t m2 = (1u << (2 * B)) - 1u;
+  constexpr uint32_t m1 = ((1u << B) - 1u) * 0x00010001u;
+  const uint32_t u = (x & m2) | ((x << (16 - 2 * B)) & (m2 << 16));
+  return (u & m1) | ((u << (8 - B)) & (m1 << 8));
+}
+
+template <int C>
+__device__ __forceinline__ uint32_t compact_c(uint32_t v) {
+  constexpr uint32_t m1 = ((1u << C) - 1u) * 0x00010001u;
+  constexpr uint32_t m1b = (((1u << C) - 1u) << C) * 0x00010001u;
+  constexpr uint32_t m2 = (1u << (2 * C)) - 1u;
+  const uint32_t u = (v & m1) | ((v >> (8 - C)) & m1b);
+  return (u & m2) | ((u >> (16 - 2 * C)) & (m2 << (2 * C)));
+}
+
+// NW consecutive shared words from word w0 (w0 a multiple of the vector
+// width chosen: 4 words when NW % 4 == 0, else 2 when even, else 1).
+template <int NW>
+__device__ __forceinline__ void lds_words(const uint32_t* buf, int w0, uint32_t* w) {
+  if constexpr (NW % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < NW / 4; ++i) {
+      const uint4 v = *reinterpret_cast<const uint4*>(buf + w0 + 4 * i);
+      w[4 * i] = v.x, w[4 * i + 1] = v.y, w[4 * i + 2] = v.z, w[4 * i + 3] = v.w;
+    }
+  } else if constexpr (NW % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < NW / 2; ++i) {
+      const uint2 v = *reinterpret_cast<const uint2*>(buf + w0 + 2 * i);
+      w[2 * i] = v.x, w[2 * i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NW; ++i) w[i] = buf[w0 + i];
+  }
+}
+
+template <int NW>
+__device__ __forceinline__ void sts_words(uint32_t* buf, int w0, const uint32_t* w) {
+  if constexpr (NW % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < NW / 4; ++i)
+      *reinterpret_cast<uint4*>(buf + w0 + 4 * i) =
+          make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+  } else if constexpr (NW % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < NW / 2; ++i)
+      *reinterpret_cast<uint2*>(buf + w0 + 2 * i) = make_uint2(w[2 * i], w[2 * i + 1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < NW; ++i) buf[w0 + i] = w[i];
+  }
+}
+
+// Registers -> shared memory in plain word order (one 16-byte store per
+// loaded vector): the staging of the byte-lane pass.
+template <int BMAX>
+__device__ __forceinline__ void stage_plain(const TileRegs<BMAX>& t, int b, uint32_t* buf,
+                                            int lane) {
+#pragma unroll
+  for (int j = 0; j < TileRegs<BMAX>::Q; ++j) {
+    const int q = lane + 32 * j;
+    if (q < 8 * b) *reinterpret_cast<uint4*>(buf + 4 * q) = t.r[j];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Operations.  produce() hands every field value of the lane's group to
 // sink(k, value) as Val<BMAX> (int32 when the class bounds every value below
@@ -133,6 +208,23 @@ struct OpAdd {
     const int64_t hi = range_hi(a.b, a.sgn) + range_hi(b.b, b.sgn);
     return range_width(lo, hi);
   }
+  // Byte lanes apply when both operands are non-negative with the same
+  // width of at most 7 bits (every sum stays below 2^8); returns that width.
+  __device__ __forceinline__ int lanes_width(int bs) const {
+    return (!a.sgn && !b.sgn && a.b == b.b && a.b <= 7 && bs <= 8) ? a.b : 0;
+  }
+  template <int BMAX>
+  __device__ __forceinline__ void lanes_stage(const Regs<BMAX>& r, uint32_t* bufa, uint32_t* bufb,
+                                              int lane) const {
+    stage_plain<BMAX>(r.ra, a.b, bufa, lane);
+    stage_plain<BMAX>(r.rb, b.b, bufb, lane);
+  }
+  // the four results of chunk c of the lane's group, one per byte
+  template <int B>
+  __device__ __forceinline__ uint32_t lanes4(const uint32_t* wa, const uint32_t* wb, int c) const {
+    return spread_c<B>(wa, c) + spread_c<B>(wb, c);
+  }
+  static constexpr bool kTwoInputs = true;
   template <int BMAX>
   __device__ __forceinline__ void prefetch(Regs<BMAX>& r, uint64_t tile, int lane) const {
     a.load(r.ra, tile, lane);
@@ -184,6 +276,21 @@ struct OpScale {
     if (lo < -lim || hi >= lim) return 65;
     return range_width((int64_t)lo, (int64_t)hi);
   }
+  // Byte lanes: A non-negative with at most 8 bits, s >= 1, every product
+  // below 2^8 (so the result width is at least A's); returns A's width.
+  __device__ __forceinline__ int lanes_width(int bs) const {
+    return (!a.sgn && s >= 1 && a.b <= 8 && bs <= 8) ? a.b : 0;
+  }
+  template <int BMAX>
+  __device__ __forceinline__ void lanes_stage(const Regs<BMAX>& r, uint32_t* bufa, uint32_t*,
+                                              int lane) const {
+    stage_plain<BMAX>(r.ra, a.b, bufa, lane);
+  }
+  template <int B>
+  __device__ __forceinline__ uint32_t lanes4(const uint32_t* wa, const uint32_t*, int c) const {
+    return spread_c<B>(wa, c) * (uint32_t)s;
+  }
+  static constexpr bool kTwoInputs = false;
   template <int BMAX>
   __device__ __forceinline__ void prefetch(Regs<BMAX>& r, uint64_t tile, int lane) const {
     a.load(r.ra, tile, lane);
@@ -211,6 +318,121 @@ struct OpScale {
 // and returns after the header when the exact width is the speculative one.
 constexpr int kStats = 0, kPack = 1, kSpec = 2;
 
+// The speculative pass on byte lanes, a kernel of its own (few registers,
+// small buffers: many warps per SM) launched before k_ew<..., kSpec>: when the
+// operands qualify (Op::lanes_width, decided from the headers), it does the
+// pass and marks the output header (reserved1 = 1) so that the general kSpec
+// launch returns at once; otherwise it returns and the general pass runs.
+// Input width B and output width BS are compile-time (add: BS = B + 1;
+// scale: B <= BS <= 8).  Per tile the inputs are staged in plain word order
+// (16-byte stores); each lane reads its group's B words with the widest
+// aligned vector, forms the results four at a time (one byte each: an add
+// or a multiply of four fields at once), ORs them into the statistics (the
+// result is non-negative: no fold, no sign), compacts them into its BS
+// output words and stores those; the warp then writes the output tile with
+// 16-byte stores.
+constexpr int kLaneRegion = 256;  // a tile of width <= 8
+
+template <class Op, int B, int BS>
+__device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t* words,
+                                        uint64_t n, uint32_t* bufa, uint32_t* bufb,
+                                        uint32_t* obuf) {
+  const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+  const uint64_t dw = data_words(n, BS);
+  const uint64_t ntiles = (n + kTile - 1) / kTile;
+  const uint64_t gwarps = (uint64_t)gridDim.x * kWarps;
+  uint32_t orb = 0;
+  uint64_t tile = (uint64_t)blockIdx.x * kWarps + warp;
+  typename Op::template Regs<8> cur, nxt;
+  if (tile < ntiles) op.template prefetch<8>(cur, tile, lane);
+  for (; tile < ntiles; tile += gwarps) {
+    if (tile + gwarps < ntiles) op.template prefetch<8>(nxt, tile + gwarps, lane);
+    op.template lanes_stage<8>(cur, bufa, bufb, lane);
+    __syncwarp();
+    uint32_t wa[B + 1], wb[B + 1];
+    lds_words<B>(bufa, lane * B, wa);
+    wa[B] = 0;
+    if constexpr (Op::kTwoInputs) {
+      lds_words<B>(bufb, lane * B, wb);
+      wb[B] = 0;
+    }
+    uint32_t ow[BS + 1];
+#pragma unroll
+    for (int i = 0; i <= BS; ++i) ow[i] = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const uint32_t r = op.template lanes4<B>(wa, wb, c);
+      orb |= r;
+      const uint32_t t = compact_c<BS>(r);
+      const int bit = 4 * BS * c, wi = bit >> 5, sh = bit & 31;
+      ow[wi] |= t << sh;
+      if (sh + 4 * BS > 32) ow[wi + 1] |= t >> (32 - sh);
+    }
+    sts_words<BS>(obuf, lane * BS, ow);
+    __syncwarp();
+    const uint64_t w0 = tile * (uint64_t)(32 * BS);
+    if (w0 + 32 * BS <= dw) {
+      uint4* dst = reinterpret_cast<uint4*>(words + w0);
+#pragma unroll
+      for (int j = 0; j < (8 * BS + 31) / 32; ++j) {
+        const int q = lane + 32 * j;
+        if (q < 8 * BS) dst[q] = *reinterpret_cast<const uint4*>(obuf + 4 * q);
+      }
+    } else {
+      const int tw = (int)(dw > w0 ? dw - w0 : 0);
+      for (int w = lane; w < tw; w += 32) words[w0 + w] = obuf[w];
+    }
+    __syncwarp();
+    cur = nxt;
+  }
+  uint32_t o = orb | (orb >> 8) | (orb >> 16) | (orb >> 24);
+  o = __reduce_or_sync(0xffffffffu, o & 0xffu);
+  if (lane == 0 && o) atomicOr(reinterpret_cast<unsigned long long*>(&out->stat_or),
+                               (unsigned long long)o);
+}
+
+// Calls lanes_body for the run-time (b, bs): add B <= 7 with BS = B + 1,
+// scale B <= BS <= 8.
+template <class Op, int B = 1, int BS = 1>
+__device__ __forceinline__ void lanes_dispatch(const Op& op, int b, int bs, ccm_header* out,
+                                               uint32_t* words, uint64_t n, uint32_t* bufa,
+                                               uint32_t* bufb, uint32_t* obuf) {
+  if constexpr (B <= 8) {
+    if constexpr (BS > 8) {
+      lanes_dispatch<Op, B + 1, B + 1>(op, b, bs, out, words, n, bufa, bufb, obuf);
+    } else {
+      constexpr bool valid = Op::kTwoInputs ? (B <= 7 && BS == B + 1) : (BS >= B);
+      if constexpr (valid) {
+        if (b == B && bs == BS) {
+          lanes_body<Op, B, BS>(op, out, words, n, bufa, bufb, obuf);
+          return;
+        }
+      }
+      lanes_dispatch<Op, B, BS + 1>(op, b, bs, out, words, n, bufa, bufb, obuf);
+    }
+  }
+}
+
+template <class Op>
+__global__ void __launch_bounds__(kThreads, 6) k_ew_lanes(Op op, ccm_header* out, uint32_t* words,
+                                                          uint64_t capacity, uint64_t n) {
+  __shared__ __align__(16) uint32_t s_buf[kWarps][3 * kLaneRegion];
+  if (out->status != CCM_OK) return;
+  op.init(n);
+  const int bs = op.spec_width();
+  const int B = (bs <= 8 && words_for(n, bs) <= capacity) ? op.lanes_width(bs) : 0;
+  if (!B) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) out->reserved1 = 1;
+  uint32_t* bufa = s_buf[threadIdx.x / kWarp];
+  lanes_dispatch<Op>(op, B, bs, out, words, n, bufa, bufa + kLaneRegion, bufa + 2 * kLaneRegion);
+}
+
+// Host launchers (ew_lanes.cu).
+void launch_lanes_add(const OpAdd& op, ccm_header* out, uint32_t* words, uint64_t capacity,
+                      uint64_t n, cudaStream_t st);
+void launch_lanes_scale(const OpScale<true>& op, ccm_header* out, uint32_t* words,
+                        uint64_t capacity, uint64_t n, cudaStream_t st);
+
 template <class Op, int BMAX, int MODE>
 __global__ void __launch_bounds__(kThreads) k_ew(Op op, ccm_header* out, uint32_t* words,
                                                  uint64_t capacity, uint64_t n, int spec) {
@@ -228,6 +450,7 @@ __global__ void __launch_bounds__(kThreads) k_ew(Op op, ccm_header* out, uint32_
     }
   } else {
     if (out->status != CCM_OK) return;
+    if (MODE == kSpec && out->reserved1) return;  // k_ew_lanes did the pass
     op.init(n);
     if constexpr (MODE == kSpec) {
       const int bs = op.spec_width();
@@ -236,6 +459,7 @@ __global__ void __launch_bounds__(kThreads) k_ew(Op op, ccm_header* out, uint32_
   }
   const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
   uint32_t* buf = s_buf[warp];
+
   const uint64_t dw = b ? data_words(n, b) : 0;
   const uint32_t mask = b >= 32 ? 0xffffffffu : ((1u << b) - 1u);
   const uint64_t ntiles = (n + kTile - 1) / kTile;
@@ -564,8 +788,10 @@ inline int ew_grid(uint64_t n, int per_sm) {
   return (int)umin(umax(want, 1), (uint64_t)num_sms() * per_sm);
 }
 
+// Returns the number of kernels launched.
 template <int C>
-void launch_ew_class(const EwCall& c, cudaStream_t st) {
+int launch_ew_class(const EwCall& c, cudaStream_t st) {
+  int launched = 1;
   const uint64_t n = c.rows * c.cols;
   PackedIn a{c.ha, c.wa, 0, 0, 0}, b{c.hb, c.wb, 0, 0, 0};
   // Persistent-style grids: every warp keeps walking tiles (and prefetching).
@@ -585,8 +811,11 @@ void launch_ew_class(const EwCall& c, cudaStream_t st) {
       const OpAdd op{a, b};
       if (c.kind == EwKind::AddStats)
         k_ew<OpAdd, C, kStats><<<g, kThreads, 0, st>>>(op, c.out, nullptr, 0, n, 0);
-      else if (c.kind == EwKind::AddSpec)
+      else if (c.kind == EwKind::AddSpec) {
+        launch_lanes_add(op, c.out, c.words, c.capacity, n, st);
+        launched = 2;
         k_ew<OpAdd, C, kSpec><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity, n, 0);
+      }
       else
         k_ew<OpAdd, C, kPack><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity, n, c.spec);
       break;
@@ -599,9 +828,14 @@ void launch_ew_class(const EwCall& c, cudaStream_t st) {
         const OpScale<true> op{a, c.s};
         if (c.kind == EwKind::ScaleStats)
           k_ew<OpScale<true>, C, kStats><<<g, kThreads, 0, st>>>(op, c.out, nullptr, 0, n, 0);
-        else if (c.kind == EwKind::ScaleSpec)
+        else if (c.kind == EwKind::ScaleSpec) {
+          if (c.s >= 1 && c.s < 256) {  // (byte lanes need 1 <= s < 2^8)
+            launch_lanes_scale(op, c.out, c.words, c.capacity, n, st);
+            launched = 2;
+          }
           k_ew<OpScale<true>, C, kSpec><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity,
                                                                 n, 0);
+        }
         else
           k_ew<OpScale<true>, C, kPack><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity,
                                                                 n, c.spec);
@@ -656,6 +890,7 @@ void launch_ew_class(const EwCall& c, cudaStream_t st) {
           c.out, c.words, c.rows, c.cols, c.capacity, (int32_t*)c.dense, c.err);
       break;
   }
+  return launched;
 }
 
 }  // namespace ge

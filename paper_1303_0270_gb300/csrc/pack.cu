@@ -9,9 +9,9 @@
 namespace ccm {
 
 namespace ge {
-extern template void launch_ew_class<8>(const EwCall& c, cudaStream_t st);
-extern template void launch_ew_class<16>(const EwCall& c, cudaStream_t st);
-extern template void launch_ew_class<32>(const EwCall& c, cudaStream_t st);
+extern template int launch_ew_class<8>(const EwCall& c, cudaStream_t st);
+extern template int launch_ew_class<16>(const EwCall& c, cudaStream_t st);
+extern template int launch_ew_class<32>(const EwCall& c, cudaStream_t st);
 }  // namespace ge
 
 int width_bound(uint64_t capacity, uint64_t n) {
@@ -32,12 +32,13 @@ namespace {
 int ew_class(int bmax) { return bmax <= 8 ? 8 : bmax <= 16 ? 16 : bmax <= 32 ? 32 : 0; }
 
 void launch_ew(int cls, const ge::EwCall& c, cudaStream_t st) {
+  int launched;
   switch (cls) {
-    case 8: ge::launch_ew_class<8>(c, st); break;
-    case 16: ge::launch_ew_class<16>(c, st); break;
-    default: ge::launch_ew_class<32>(c, st); break;
+    case 8: launched = ge::launch_ew_class<8>(c, st); break;
+    case 16: launched = ge::launch_ew_class<16>(c, st); break;
+    default: launched = ge::launch_ew_class<32>(c, st); break;
   }
-  note_launch();
+  note_launch(launched);
 }
 
 }  // namespace

@@ -280,8 +280,10 @@ def test_width_class_and_runtime_kernels_agree(ccm, b):
                                f"scale {s} b={b} cap={cap}")
 
 
-@pytest.mark.parametrize("ba,sa,bb,sb", [(5, 0, 5, 0), (7, 1, 3, 0), (3, 0, 7, 1), (8, 1, 8, 1),
-                                         (16, 1, 1, 0), (13, 0, 13, 0), (31, 1, 31, 1)])
+@pytest.mark.parametrize("ba,sa,bb,sb", [(5, 0, 5, 0), (1, 0, 1, 0), (3, 0, 4, 0), (7, 0, 7, 0),
+                                         (2, 0, 6, 0), (8, 0, 1, 0), (7, 1, 3, 0), (3, 0, 7, 1),
+                                         (8, 1, 8, 1), (16, 1, 1, 0), (13, 0, 13, 0),
+                                         (31, 1, 31, 1)])
 @pytest.mark.parametrize("hit", [True, False])
 def test_add_speculative_width(ccm, ba, sa, bb, sb, hit):
     """The one-pass add writes C at the width the input ranges bound the sum
@@ -307,11 +309,13 @@ def test_add_speculative_width(ccm, ba, sa, bb, sb, hit):
     assert_same_packed(got, expect, f"add spec {ba}/{sa} + {bb}/{sb} hit={hit}")
 
 
-@pytest.mark.parametrize("b,sgn", [(5, 0), (4, 1), (12, 1), (20, 0)])
-@pytest.mark.parametrize("s", [7, -7, 8, 1, 0, -1, 3000, -40000])
+@pytest.mark.parametrize("b,sgn", [(5, 0), (1, 0), (3, 0), (8, 0), (4, 1), (12, 1), (20, 0)])
+@pytest.mark.parametrize("s", [7, -7, 8, 1, 0, 2, -1, 3000, -40000])
 def test_scale_speculative_width(ccm, b, sgn, s):
     """One-pass scale: s times the range of A's width; the maximum entry at the
-    range top (hit) and below it (the exact width may be smaller: second pass)."""
+    range top (hit) and below it (the exact width may be smaller: second pass).
+    Non-negative A of at most 8 bits with s >= 0 and a product range within 8
+    bits takes the byte-lane pass."""
     shape = (7, 2049)
     a = _rand(b * 3 + sgn, shape, b, bool(sgn))
     for top in (True, False):
