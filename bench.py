@@ -747,6 +747,27 @@ def oracle_sample(rows: int):
     return sec, nbytes
 
 
+def _oracle_worker(rows: int):
+    return oracle_sample(rows)
+
+
+def cpu_baseline_parallel(rows: int, procs: int):
+    """The same oracle sample in `procs` processes at once (one row block per
+    core, as an OpenMP loop over rows would split it): throughput of the
+    oracle on all host cores.  Spawned processes (no fork of a CUDA parent)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        pool.map(_oracle_worker, [64] * procs)  # imports and library loads, untimed
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_worker, [rows] * procs)
+        wall = time.perf_counter() - t0
+    nb = sum(r[1] for r in res)
+    return {"value": round(nb / wall / 1e9, 4), "unit": "GB/s", "cores": procs, "kind": "oracle",
+            "sample": f"{procs} processes, each rows 0..{rows - 1} of the 8192x8192 workload "
+                      f"(same operations as the one-core sample); {wall:.1f} s wall"}
+
+
 def cpu_baseline(target_s: float = 12.0):
     sec, nb = oracle_sample(64)
     rows = int(min(N_ROWS, max(64, 64 * target_s / max(sec, 1e-3))))
@@ -828,6 +849,12 @@ def main():
     if line is not None:
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
+            procs = max(1, os.cpu_count() or 1)
+            if procs > 1:
+                # per process about as much work as the one-core sample
+                rows1 = int(line["cpu_baseline"]["sample"].split("rows 0..")[1].split(" ")[0]) + 1
+                line["cpu_baseline_all_cores"] = cpu_baseline_parallel(
+                    max(64, rows1 // 64 * 64), procs)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
