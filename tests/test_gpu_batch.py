@@ -25,7 +25,17 @@ def _batch_inputs(seed, count, lo=1, hi=300, wlo=1, whi=24):
         a = synth.uniform_signed(s, synth.STREAM_A, int(rows[i] * cols[i]), b)
         if i % 3 == 0:
             a = np.abs(a)  # unsigned fields too
-        x = synth.uniform_signed(s, synth.STREAM_X, int(cols[i]), 8)
+        # x kinds: signed 8-bit (byte lanes for b <= 8), unsigned 7-bit (byte
+        # lanes), unsigned 8-bit and signed 12-bit (the int32 path at any b)
+        xk = i % 4
+        if xk == 0:
+            x = synth.uniform_signed(s, synth.STREAM_X, int(cols[i]), 8)
+        elif xk == 1:
+            x = synth.uniform_int(s, synth.STREAM_X, int(cols[i]), 0, 127)
+        elif xk == 2:
+            x = synth.uniform_int(s, synth.STREAM_X, int(cols[i]), 0, 255)
+        else:
+            x = synth.uniform_signed(s, synth.STREAM_X, int(cols[i]), 12)
         mats.append(a.reshape(int(rows[i]), int(cols[i])))
         xs.append(x.reshape(-1, 1))
     return mats, xs
