@@ -74,6 +74,9 @@ struct PackedIn {
       t.r[j] = v;
     }
   }
+  // Global -> shared in plain word order with 16-byte cp.async (zero past
+  // the data words), for the byte-lane pass (b <= 8: 8b <= 64 vectors).
+  __device__ __forceinline__ void issue_tile(uint64_t tile, uint32_t* buf, int lane) const;
   // Registers -> shared staging layout.
   template <int BMAX>
   __device__ __forceinline__ void stage(const TileRegs<BMAX>& t, uint32_t* buf, int lane) const {
@@ -105,6 +108,39 @@ __device__ __forceinline__ int range_width(int64_t lo, int64_t hi) {
   if (lo >= 0) return h > 1 ? h : 1;
   const int l = bitlen64((uint64_t)~lo);
   return 1 + (h > l ? h : l);
+}
+
+// cp.async helpers (16 bytes, zero-filled past `bytes`; commit; wait).
+__device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, uint32_t bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_ge() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait1_ge() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait0_ge() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait2_ge() {
+  asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void PackedIn::issue_tile(uint64_t tile, uint32_t* buf,
+                                                    int lane) const {
+  const uint64_t w0 = tile * (uint64_t)(32 * b);
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int q = lane + 32 * j;
+    if (q < 8 * b) {
+      const uint64_t g = w0 + 4 * (uint64_t)q;
+      const uint32_t bytes = g + 4 <= dw ? 16u : (g < dw ? (uint32_t)(dw - g) * 4u : 0u);
+      cp_async16_zfill(buf + 4 * q, w + (bytes ? g : 0), bytes);
+    }
+  }
 }
 
 // Byte lanes: four fields of at most 8 bits in one 32-bit register, field k
@@ -170,17 +206,6 @@ __device__ __forceinline__ void sts_words(uint32_t* buf, int w0, const uint32_t*
   }
 }
 
-// Registers -> shared memory in plain word order (one 16-byte store per
-// loaded vector): the staging of the byte-lane pass.
-template <int BMAX>
-__device__ __forceinline__ void stage_plain(const TileRegs<BMAX>& t, int b, uint32_t* buf,
-                                            int lane) {
-#pragma unroll
-  for (int j = 0; j < TileRegs<BMAX>::Q; ++j) {
-    const int q = lane + 32 * j;
-    if (q < 8 * b) *reinterpret_cast<uint4*>(buf + 4 * q) = t.r[j];
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Operations.  produce() hands every field value of the lane's group to
@@ -213,18 +238,18 @@ struct OpAdd {
   __device__ __forceinline__ int lanes_width(int bs) const {
     return (!a.sgn && !b.sgn && a.b == b.b && a.b <= 7 && bs <= 8) ? a.b : 0;
   }
-  template <int BMAX>
-  __device__ __forceinline__ void lanes_stage(const Regs<BMAX>& r, uint32_t* bufa, uint32_t* bufb,
-                                              int lane) const {
-    stage_plain<BMAX>(r.ra, a.b, bufa, lane);
-    stage_plain<BMAX>(r.rb, b.b, bufb, lane);
-  }
   // the four results of chunk c of the lane's group, one per byte
   template <int B>
   __device__ __forceinline__ uint32_t lanes4(const uint32_t* wa, const uint32_t* wb, int c) const {
     return spread_c<B>(wa, c) + spread_c<B>(wb, c);
   }
   static constexpr bool kTwoInputs = true;
+  // cp.async of tile `tile` of both inputs into plain-order shared buffers
+  __device__ __forceinline__ void lanes_issue(uint64_t tile, uint32_t* bufa, uint32_t* bufb,
+                                              int lane) const {
+    a.issue_tile(tile, bufa, lane);
+    b.issue_tile(tile, bufb, lane);
+  }
   template <int BMAX>
   __device__ __forceinline__ void prefetch(Regs<BMAX>& r, uint64_t tile, int lane) const {
     a.load(r.ra, tile, lane);
@@ -281,16 +306,15 @@ struct OpScale {
   __device__ __forceinline__ int lanes_width(int bs) const {
     return (!a.sgn && s >= 1 && a.b <= 8 && bs <= 8) ? a.b : 0;
   }
-  template <int BMAX>
-  __device__ __forceinline__ void lanes_stage(const Regs<BMAX>& r, uint32_t* bufa, uint32_t*,
-                                              int lane) const {
-    stage_plain<BMAX>(r.ra, a.b, bufa, lane);
-  }
   template <int B>
   __device__ __forceinline__ uint32_t lanes4(const uint32_t* wa, const uint32_t*, int c) const {
     return spread_c<B>(wa, c) * (uint32_t)s;
   }
   static constexpr bool kTwoInputs = false;
+  __device__ __forceinline__ void lanes_issue(uint64_t tile, uint32_t* bufa, uint32_t*,
+                                              int lane) const {
+    a.issue_tile(tile, bufa, lane);
+  }
   template <int BMAX>
   __device__ __forceinline__ void prefetch(Regs<BMAX>& r, uint64_t tile, int lane) const {
     a.load(r.ra, tile, lane);
@@ -332,28 +356,43 @@ constexpr int kStats = 0, kPack = 1, kSpec = 2;
 // output words and stores those; the warp then writes the output tile with
 // 16-byte stores.
 constexpr int kLaneRegion = 256;  // a tile of width <= 8
+constexpr int kLaneStages = 3;    // cp.async ring depth of the byte-lane pass
 
 template <class Op, int B, int BS>
 __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t* words,
-                                        uint64_t n, uint32_t* bufa, uint32_t* bufb,
-                                        uint32_t* obuf) {
+                                        uint64_t n, uint32_t* sbuf) {
   const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
   const uint64_t dw = data_words(n, BS);
   const uint64_t ntiles = (n + kTile - 1) / kTile;
   const uint64_t gwarps = (uint64_t)gridDim.x * kWarps;
+  const uint64_t tile0 = (uint64_t)blockIdx.x * kWarps + warp;
+  // per warp: kLaneStages slots of (A tile, B tile), then the output tile
+  uint32_t* obuf = sbuf + kLaneStages * 2 * kLaneRegion;
+  auto slot_a = [&](uint32_t k) { return sbuf + (k % kLaneStages) * 2 * kLaneRegion; };
   uint32_t orb = 0;
-  uint64_t tile = (uint64_t)blockIdx.x * kWarps + warp;
-  typename Op::template Regs<8> cur, nxt;
-  if (tile < ntiles) op.template prefetch<8>(cur, tile, lane);
-  for (; tile < ntiles; tile += gwarps) {
-    if (tile + gwarps < ntiles) op.template prefetch<8>(nxt, tile + gwarps, lane);
-    op.template lanes_stage<8>(cur, bufa, bufb, lane);
+  // cp.async ring: tiles k + 1 and k + 2 in flight while tile k is decoded
+#pragma unroll
+  for (uint32_t k = 0; k < kLaneStages - 1; ++k) {
+    const uint64_t t = tile0 + k * gwarps;
+    if (t < ntiles) op.lanes_issue(t, slot_a(k), slot_a(k) + kLaneRegion, lane);
+    cp_async_commit_ge();
+  }
+  for (uint32_t k = 0;; ++k) {
+    const uint64_t tile = tile0 + k * gwarps;
+    if (tile >= ntiles) break;
+    const uint64_t tn = tile + (kLaneStages - 1) * gwarps;
+    if (tn < ntiles)
+      op.lanes_issue(tn, slot_a(k + kLaneStages - 1), slot_a(k + kLaneStages - 1) + kLaneRegion,
+                     lane);
+    cp_async_commit_ge();
+    cp_async_wait2_ge();  // tile k has landed (groups complete in order)
     __syncwarp();
+    const uint32_t* bufa = slot_a(k);
     uint32_t wa[B + 1], wb[B + 1];
     lds_words<B>(bufa, lane * B, wa);
     wa[B] = 0;
     if constexpr (Op::kTwoInputs) {
-      lds_words<B>(bufb, lane * B, wb);
+      lds_words<B>(bufa + kLaneRegion, lane * B, wb);
       wb[B] = 0;
     }
     uint32_t ow[BS + 1];
@@ -383,8 +422,8 @@ __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t*
       for (int w = lane; w < tw; w += 32) words[w0 + w] = obuf[w];
     }
     __syncwarp();
-    cur = nxt;
   }
+  cp_async_wait0_ge();
   uint32_t o = orb | (orb >> 8) | (orb >> 16) | (orb >> 24);
   o = __reduce_or_sync(0xffffffffu, o & 0xffu);
   if (lane == 0 && o) atomicOr(reinterpret_cast<unsigned long long*>(&out->stat_or),
@@ -395,36 +434,34 @@ __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t*
 // scale B <= BS <= 8.
 template <class Op, int B = 1, int BS = 1>
 __device__ __forceinline__ void lanes_dispatch(const Op& op, int b, int bs, ccm_header* out,
-                                               uint32_t* words, uint64_t n, uint32_t* bufa,
-                                               uint32_t* bufb, uint32_t* obuf) {
+                                               uint32_t* words, uint64_t n, uint32_t* sbuf) {
   if constexpr (B <= 8) {
     if constexpr (BS > 8) {
-      lanes_dispatch<Op, B + 1, B + 1>(op, b, bs, out, words, n, bufa, bufb, obuf);
+      lanes_dispatch<Op, B + 1, B + 1>(op, b, bs, out, words, n, sbuf);
     } else {
       constexpr bool valid = Op::kTwoInputs ? (B <= 7 && BS == B + 1) : (BS >= B);
       if constexpr (valid) {
         if (b == B && bs == BS) {
-          lanes_body<Op, B, BS>(op, out, words, n, bufa, bufb, obuf);
+          lanes_body<Op, B, BS>(op, out, words, n, sbuf);
           return;
         }
       }
-      lanes_dispatch<Op, B, BS + 1>(op, b, bs, out, words, n, bufa, bufb, obuf);
+      lanes_dispatch<Op, B, BS + 1>(op, b, bs, out, words, n, sbuf);
     }
   }
 }
 
 template <class Op>
-__global__ void __launch_bounds__(kThreads, 6) k_ew_lanes(Op op, ccm_header* out, uint32_t* words,
-                                                          uint64_t capacity, uint64_t n) {
-  __shared__ __align__(16) uint32_t s_buf[kWarps][3 * kLaneRegion];
+__global__ void __launch_bounds__(kThreads) k_ew_lanes(Op op, ccm_header* out, uint32_t* words,
+                                                       uint64_t capacity, uint64_t n) {
+  __shared__ __align__(16) uint32_t s_buf[kWarps][(2 * kLaneStages + 1) * kLaneRegion];
   if (out->status != CCM_OK) return;
   op.init(n);
   const int bs = op.spec_width();
   const int B = (bs <= 8 && words_for(n, bs) <= capacity) ? op.lanes_width(bs) : 0;
   if (!B) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) out->reserved1 = 1;
-  uint32_t* bufa = s_buf[threadIdx.x / kWarp];
-  lanes_dispatch<Op>(op, B, bs, out, words, n, bufa, bufa + kLaneRegion, bufa + 2 * kLaneRegion);
+  lanes_dispatch<Op>(op, B, bs, out, words, n, s_buf[threadIdx.x / kWarp]);
 }
 
 // Host launchers (ew_lanes.cu).
@@ -549,21 +586,6 @@ __global__ void __launch_bounds__(kThreads) k_pack_dense(const T* __restrict__ s
 // the end): the next tile is in flight while the warp packs the current one.
 // Shared layout: element f at f + 2*(f/32) (keeps 16-byte alignment; the
 // lane's 16-byte reads of its 32 elements are conflict-free).
-__device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, uint32_t bytes) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit_ge() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait1_ge() {
-  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait0_ge() {
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-}
-
 constexpr int kDensePad = kTile + 2 * (kTile / 32);  // int64 slots per staged tile
 
 __device__ __forceinline__ void issue_dense_tile(int64_t* dst, const int64_t* __restrict__ src,
