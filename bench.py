@@ -510,10 +510,31 @@ def run_matmul_bench(args, rank, world, local_rank):
             "cudacore_useful_int_TOPS": round(useful / (timings["cudacore"][0] * 1e-3) / 1e12, 3),
             "speedup_tensor_vs_cudacore": round(timings["cudacore"][0] / t_all, 2),
         })
+    # reference point: a plain s8 x s8 -> s32 GEMM of the same size through
+    # the vendor library (torch._int_mm -> cuBLASLt), the integer tensor rate
+    # an int8-limb design would get on this GPU
+    int8_tops = None
+    try:
+        a8 = torch.randint(-128, 128, (n, n), dtype=torch.int8, device=dev)
+        b8 = torch.randint(-128, 128, (n, n), dtype=torch.int8, device=dev)
+        for _ in range(3):
+            torch._int_mm(a8, b8)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            torch._int_mm(a8, b8)
+        e1.record()
+        e1.synchronize()
+        int8_tops = round(2.0 * n ** 3 / (e0.elapsed_time(e1) / 10 * 1e-3) / 1e12, 1)
+    except RuntimeError:
+        pass
     return {"metric": METRIC, "workload": "packed matmul", "unit": "int-TOPS (useful)",
             "value": round(statistics.mean(r["useful_int_TOPS"] for r in results), 2),
             "n": n, "fp8_peak_TFLOPS": fp8_peak,
             "fp8_peak_source": "MEASURED_PEAKS bf16_tflops x 2 (nominal fp8/bf16 ratio)",
+            "s8_gemm_library_TOPS": int8_tops,
+            "s8_gemm_library": "torch._int_mm (cuBLASLt) s8 x s8 -> s32, same n, 10 launches",
             "results": results}
 
 
