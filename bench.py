@@ -637,6 +637,83 @@ def run_vlb_bench(args, rank, world, local_rank):
             "results": results}
 
 
+def run_sweep_bench(args, rank, world, local_rank):
+    """The width sweep of the 8192 x 8192 workload: for each b, A and B with
+    entries uniform over the signed b-bit range (generated on the GPU), x
+    signed 8-bit; pack (single pass), unpack, A + B, 7A and A x, each timed
+    on its main kernel(s) with L2 flushed before every repetition, as GB/s of
+    algorithmic bytes and as a fraction of the measured HBM peak."""
+    import torch
+
+    import synth
+    from paper_1303_0270_gb300 import ccm
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    n_rows = n_cols = 8192
+    n = n_rows * n_cols
+    hbm, _ = peaks()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    X = ccm.gen_uniform(n_cols, SEED_A, synth.STREAM_X, -128, 127, device=dev).view(n_cols, 1)
+    px = ccm.pack(X)
+    A = torch.empty((n_rows, n_cols), dtype=torch.int64, device=dev)
+    B = torch.empty_like(A)
+    unp = torch.empty_like(A)
+    reps = max(3, args.steps)
+
+    def kernel_ms(fn):
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0.record()
+        k1.record()
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for i in range(reps):
+            flush.fill_(i & 255)
+            ccm.profile_next(k0, k1)
+            fn()
+            torch.cuda.synchronize()
+            ts.append(k0.elapsed_time(k1))
+        return statistics.mean(ts)
+
+    rows = []
+    widths = [int(w) for w in args.sweep_widths.split(",")]
+    for b in widths:
+        lo, hi = synth.signed_range(b)
+        ccm.gen_uniform(n, SEED_A + b, synth.STREAM_A, lo, hi, out=A.view(-1))
+        ccm.gen_uniform(n, SEED_B + b, synth.STREAM_B, lo, hi, out=B.view(-1))
+        pa = ccm.PackedMatrix(n_rows, n_cols, ccm.words_for(n_rows, n_cols, b), dev)
+        pb = ccm.PackedMatrix(n_rows, n_cols, ccm.words_for(n_rows, n_cols, b), dev)
+        ws = ccm.workspace(ccm.OP_PACK, n_rows, n_cols, pa.capacity, dev)
+        ccm.pack_into(B, pb, ws=ws)
+        pc = ccm.PackedMatrix(n_rows, n_cols, ccm.words_for(n_rows, n_cols, min(64, b + 2)), dev)
+        pd = ccm.PackedMatrix(n_rows, n_cols, ccm.words_for(n_rows, n_cols, min(64, b + 4)), dev)
+        py = ccm.PackedMatrix(n_rows, 1, ccm.words_for(n_rows, 1, 64), dev)
+        wsm = ccm.workspace(ccm.OP_MATVEC, n_rows, n_cols, 1, dev)
+        t = {"pack": kernel_ms(lambda: ccm.pack_into(A, pa, ws=ws)),
+             "unpack": kernel_ms(lambda: ccm.unpack(pa, out=unp, check=False)),
+             "add": kernel_ms(lambda: ccm.add_into(pa, pb, pc)),
+             "scale": kernel_ms(lambda: ccm.scale_into(pa, SCALE, pd)),
+             "matvec": kernel_ms(lambda: ccm.matvec_into(pa, px, py, ws=wsm))}
+        assert pa.check().width == b and torch.equal(unp, A)
+        bc, bd, by = pc.check().width, pd.check().width, py.check().width
+        nb = {"pack": 8 * n + n * b / 8, "unpack": n * b / 8 + 8 * n,
+              "add": n * (2 * b + bc) / 8, "scale": n * (b + bd) / 8,
+              "matvec": n * b / 8 + n_cols + n_rows * by / 8}
+        gbs = {k: nb[k] / (t[k] * 1e-3) / 1e9 for k in t}
+        rows.append({"b": b, "ms": {k: round(v, 4) for k, v in t.items()},
+                     "GB/s": {k: round(v, 1) for k, v in gbs.items()},
+                     "frac_of_hbm": {k: round(v / hbm, 3) for k, v in gbs.items()}})
+        del pa, pb, pc, pd, py, ws, wsm
+        torch.cuda.empty_cache()
+    mv = statistics.mean(r["GB/s"]["matvec"] for r in rows)
+    return {"metric": METRIC, "workload": "width sweep", "unit": "GB/s", "value": round(mv, 1),
+            "value_is": "mean matvec GB/s over the swept widths", "frac_of_hbm": round(mv / hbm, 4),
+            "config": {"workload": "8192x8192, entries uniform over the signed b-bit range, "
+                                   "x signed 8-bit, s = 7", "widths": widths,
+                       "l2": "flushed (256 MiB write) before every repetition"},
+            "results": rows}
+
+
 def run_serve_bench(args, rank, world, local_rank):
     """Serving: a store of packed matrices (dims log-uniform in [64, 8192),
     widths U{2..20}) resident on the GPU, a Poisson stream of requests (60 %
@@ -866,7 +943,8 @@ def main():
     ap.add_argument("--impl", default="ccm", choices=["ccm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="step",
-                    choices=["step", "batch", "matmul", "serve", "vlb"])
+                    choices=["step", "batch", "matmul", "serve", "vlb", "sweep"])
+    ap.add_argument("--sweep-widths", default="1,2,3,4,5,6,7,8,10,12,16,20,24,28,31,32")
     ap.add_argument("--store-gb", type=float, default=8.0)
     ap.add_argument("--serve-budget-gb", type=float, default=16.0)
     ap.add_argument("--serve-requests", type=int, default=2000)
@@ -890,9 +968,9 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    if args.workload in ("batch", "matmul", "serve", "vlb"):
+    if args.workload in ("batch", "matmul", "serve", "vlb", "sweep"):
         fn = {"batch": run_batch, "matmul": run_matmul_bench, "serve": run_serve_bench,
-              "vlb": run_vlb_bench}[args.workload]
+              "vlb": run_vlb_bench, "sweep": run_sweep_bench}[args.workload]
         line = fn(args, rank, world, local_rank)
         if rank == 0:
             print(json.dumps(line), flush=True)

@@ -75,7 +75,8 @@ struct PackedIn {
     }
   }
   // Global -> shared in plain word order with 16-byte cp.async (zero past
-  // the data words), for the byte-lane pass (b <= 8: 8b <= 64 vectors).
+  // the data words), for the lane pass at compile-time width B (= b).
+  template <int B>
   __device__ __forceinline__ void issue_tile(uint64_t tile, uint32_t* buf, int lane) const;
   // Registers -> shared staging layout.
   template <int BMAX>
@@ -129,13 +130,14 @@ __device__ __forceinline__ void cp_async_wait2_ge() {
   asm volatile("cp.async.wait_group 2;\n" ::: "memory");
 }
 
+template <int B>
 __device__ __forceinline__ void PackedIn::issue_tile(uint64_t tile, uint32_t* buf,
                                                     int lane) const {
-  const uint64_t w0 = tile * (uint64_t)(32 * b);
+  const uint64_t w0 = tile * (uint64_t)(32 * B);
 #pragma unroll
-  for (int j = 0; j < 2; ++j) {
+  for (int j = 0; j < (8 * B + 31) / 32; ++j) {
     const int q = lane + 32 * j;
-    if (q < 8 * b) {
+    if (q < 8 * B) {
       const uint64_t g = w0 + 4 * (uint64_t)q;
       const uint32_t bytes = g + 4 <= dw ? 16u : (g < dw ? (uint32_t)(dw - g) * 4u : 0u);
       cp_async16_zfill(buf + 4 * q, w + (bytes ? g : 0), bytes);
@@ -165,6 +167,54 @@ __device__ __forceinline__ uint32_t compact_c(uint32_t v) {
   constexpr uint32_t m2 = (1u << (2 * C)) - 1u;
   const uint32_t u = (v & m1) | ((v >> (8 - C)) & m1b);
   return (u & m2) | ((u >> (16 - 2 * C)) & (m2 << (2 * C)));
+}
+
+// Lanes of L = 8, 16 or 32 bits: K = 32 / L fields per register.  spread_l
+// moves the K fields of chunk c (fields K c .. K c + K - 1 of a B-bit group)
+// into the lanes; compact_l is the inverse at width C.
+template <int L>
+__host__ __device__ constexpr uint32_t lane_ones() {
+  return L == 8 ? 0x01010101u : (L == 16 ? 0x00010001u : 1u);
+}
+
+template <int B, int L>
+__device__ __forceinline__ uint32_t spread_l(const uint32_t* w, int c) {
+  if constexpr (L == 8) {
+    return spread_c<B>(w, c);
+  } else {
+    constexpr int K = 32 / L;
+    constexpr uint32_t lo = B >= 32 ? ~0u : (1u << B) - 1u;
+    const int bit = K * B * c, wi = bit >> 5, sh = bit & 31;
+    const uint32_t x = sh + K * B <= 32 ? (w[wi] >> sh) : __funnelshift_r(w[wi], w[wi + 1], sh);
+    if constexpr (L == 16)
+      return (x & lo) | ((x << (16 - B)) & (lo << 16));
+    else
+      return x & lo;
+  }
+}
+
+template <int C, int L>
+__device__ __forceinline__ uint32_t compact_l(uint32_t v) {
+  if constexpr (L == 8) {
+    return compact_c<C>(v);
+  } else if constexpr (L == 16) {
+    constexpr uint32_t lo = (1u << C) - 1u;
+    return (v & lo) | ((v >> (16 - C)) & (lo << C));
+  } else {
+    return v;
+  }
+}
+
+// Positions of the sign bits of the 32 fields of a B-bit group that fall in
+// word i of the group (the word-level XOR that turns two's complement fields
+// into offset binary, u = a + 2^(B-1)).
+__host__ __device__ constexpr uint32_t group_sign_bits(int B, int i) {
+  uint32_t m = 0;
+  for (int e = 0; e < 32; ++e) {
+    const int p = e * B + B - 1;
+    if ((p >> 5) == i) m |= 1u << (p & 31);
+  }
+  return m;
 }
 
 // NW consecutive shared words from word w0 (w0 a multiple of the vector
@@ -233,22 +283,42 @@ struct OpAdd {
     const int64_t hi = range_hi(a.b, a.sgn) + range_hi(b.b, b.sgn);
     return range_width(lo, hi);
   }
-  // Byte lanes apply when both operands are non-negative with the same
-  // width of at most 7 bits (every sum stays below 2^8); returns that width.
+  // Lanes apply when both operands have the same width B <= 31 and sign
+  // mode: the sum then needs B + 1 bits (the speculative width) and fits a
+  // lane of 8, 16 or 32 bits.  Returns B (0: not applicable).
   __device__ __forceinline__ int lanes_width(int bs) const {
-    return (!a.sgn && !b.sgn && a.b == b.b && a.b <= 7 && bs <= 8) ? a.b : 0;
+    return (a.sgn == b.sgn && a.b == b.b && a.b <= 31 && bs == a.b + 1) ? a.b : 0;
   }
-  // the four results of chunk c of the lane's group, one per byte
-  template <int B>
-  __device__ __forceinline__ uint32_t lanes4(const uint32_t* wa, const uint32_t* wb, int c) const {
-    return spread_c<B>(wa, c) + spread_c<B>(wb, c);
+  __device__ __forceinline__ int lanes_sign() const { return a.sgn; }
+  // Chunk c of the lane's group: the sums, one per lane, as the output
+  // field bits (width B + 1), with the statistics of the result.  Signed
+  // inputs arrive in offset binary (u = a + 2^(B-1)), so s = u_a + u_b =
+  // c + 2^B: c >= 0 exactly when bit B of s is set, the output bits are
+  // s ^ 2^B, and the folded value (c >= 0 ? c : ~c) is s or ~s below bit B.
+  template <int B, int L, bool SGN>
+  __device__ __forceinline__ uint32_t lanes_k(const uint32_t* wa, const uint32_t* wb, int c,
+                                              uint32_t& orb, uint32_t& neg) const {
+    const uint32_t sum = spread_l<B, L>(wa, c) + spread_l<B, L>(wb, c);
+    if constexpr (!SGN) {
+      orb |= sum;
+      return sum;
+    } else {
+      constexpr uint32_t ones = lane_ones<L>();
+      constexpr uint32_t lo = (B >= 32 ? ~0u : (1u << B) - 1u) * ones;
+      constexpr uint32_t bitb = (1u << B) * ones;
+      const uint32_t pos = ((sum >> B) & ones) * (lo / ones);  // lanes with c >= 0
+      orb |= (sum ^ lo ^ pos) & lo;
+      neg |= ~sum & bitb;
+      return sum ^ bitb;
+    }
   }
   static constexpr bool kTwoInputs = true;
   // cp.async of tile `tile` of both inputs into plain-order shared buffers
+  template <int B>
   __device__ __forceinline__ void lanes_issue(uint64_t tile, uint32_t* bufa, uint32_t* bufb,
                                               int lane) const {
-    a.issue_tile(tile, bufa, lane);
-    b.issue_tile(tile, bufb, lane);
+    a.template issue_tile<B>(tile, bufa, lane);
+    b.template issue_tile<B>(tile, bufb, lane);
   }
   template <int BMAX>
   __device__ __forceinline__ void prefetch(Regs<BMAX>& r, uint64_t tile, int lane) const {
@@ -306,14 +376,19 @@ struct OpScale {
   __device__ __forceinline__ int lanes_width(int bs) const {
     return (!a.sgn && s >= 1 && a.b <= 8 && bs <= 8) ? a.b : 0;
   }
-  template <int B>
-  __device__ __forceinline__ uint32_t lanes4(const uint32_t* wa, const uint32_t*, int c) const {
-    return spread_c<B>(wa, c) * (uint32_t)s;
+  __device__ __forceinline__ int lanes_sign() const { return 0; }
+  template <int B, int L, bool SGN>
+  __device__ __forceinline__ uint32_t lanes_k(const uint32_t* wa, const uint32_t*, int c,
+                                              uint32_t& orb, uint32_t&) const {
+    const uint32_t r = spread_l<B, L>(wa, c) * (uint32_t)s;
+    orb |= r;
+    return r;
   }
   static constexpr bool kTwoInputs = false;
+  template <int B>
   __device__ __forceinline__ void lanes_issue(uint64_t tile, uint32_t* bufa, uint32_t*,
                                               int lane) const {
-    a.issue_tile(tile, bufa, lane);
+    a.template issue_tile<B>(tile, bufa, lane);
   }
   template <int BMAX>
   __device__ __forceinline__ void prefetch(Regs<BMAX>& r, uint64_t tile, int lane) const {
@@ -342,70 +417,90 @@ struct OpScale {
 // and returns after the header when the exact width is the speculative one.
 constexpr int kStats = 0, kPack = 1, kSpec = 2;
 
-// The speculative pass on byte lanes, a kernel of its own (few registers,
-// small buffers: many warps per SM) launched before k_ew<..., kSpec>: when the
-// operands qualify (Op::lanes_width, decided from the headers), it does the
-// pass and marks the output header (reserved1 = 1) so that the general kSpec
-// launch returns at once; otherwise it returns and the general pass runs.
-// Input width B and output width BS are compile-time (add: BS = B + 1;
-// scale: B <= BS <= 8).  Per tile the inputs are staged in plain word order
-// (16-byte stores); each lane reads its group's B words with the widest
-// aligned vector, forms the results four at a time (one byte each: an add
-// or a multiply of four fields at once), ORs them into the statistics (the
-// result is non-negative: no fold, no sign), compacts them into its BS
-// output words and stores those; the warp then writes the output tile with
-// 16-byte stores.
-constexpr int kLaneRegion = 256;  // a tile of width <= 8
-constexpr int kLaneStages = 3;    // cp.async ring depth of the byte-lane pass
+// The speculative pass on lanes, a kernel of its own (few registers, buffers
+// sized to the operands: many warps per SM) launched before k_ew<..., kSpec>:
+// when the operands qualify (Op::lanes_width, decided from the headers), it
+// does the pass and marks the output header (reserved1 = 1) so that the
+// general kSpec launch returns at once; otherwise it returns and the general
+// pass runs.  Input width B, output width BS, lane size L (8, 16 or 32 bits:
+// four, two or one field per register) and sign mode are compile-time.
+// Per tile the inputs are staged in plain word order through a cp.async
+// ring; each lane reads its group's B words with the widest aligned vector
+// (signed inputs: XOR of the sign bits), forms the results a register of
+// lanes at a time (one add or multiply for 4, 2 or 1 fields), ORs the
+// statistics, compacts the results into its BS output words and stores
+// those; the warp then writes the output tile with 16-byte stores.
+__host__ __device__ constexpr int lane_stages(int B) { return B <= 8 ? 3 : 2; }
 
-template <class Op, int B, int BS>
+// Shared words per warp for input widths up to bmax (the largest over
+// b <= bmax of the ring and the output tile of width b + 1).
+__host__ __device__ constexpr uint32_t lane_warp_words(int bmax) {
+  uint32_t m = 0;
+  for (int b = 1; b <= bmax; ++b) {
+    const uint32_t v = (uint32_t)(lane_stages(b) * 2 * 32 * b + 32 * (b + 1));
+    if (v > m) m = v;
+  }
+  return m;
+}
+
+template <class Op, int B, int BS, int L, bool SGN>
 __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t* words,
                                         uint64_t n, uint32_t* sbuf) {
+  constexpr int S = lane_stages(B);
+  constexpr int TW = 32 * B;  // words of an input tile
+  constexpr int K = 32 / L;   // fields per register
   const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
   const uint64_t dw = data_words(n, BS);
   const uint64_t ntiles = (n + kTile - 1) / kTile;
   const uint64_t gwarps = (uint64_t)gridDim.x * kWarps;
   const uint64_t tile0 = (uint64_t)blockIdx.x * kWarps + warp;
-  // per warp: kLaneStages slots of (A tile, B tile), then the output tile
-  uint32_t* obuf = sbuf + kLaneStages * 2 * kLaneRegion;
-  auto slot_a = [&](uint32_t k) { return sbuf + (k % kLaneStages) * 2 * kLaneRegion; };
-  uint32_t orb = 0;
-  // cp.async ring: tiles k + 1 and k + 2 in flight while tile k is decoded
+  // per warp: S slots of (A tile, B tile), then the output tile
+  uint32_t* obuf = sbuf + S * 2 * TW;
+  auto slot_a = [&](uint32_t k) { return sbuf + (k % S) * 2 * TW; };
+  uint32_t orb = 0, neg = 0;
+  // cp.async ring: the next S - 1 tiles in flight while tile k is decoded
 #pragma unroll
-  for (uint32_t k = 0; k < kLaneStages - 1; ++k) {
+  for (uint32_t k = 0; k < S - 1; ++k) {
     const uint64_t t = tile0 + k * gwarps;
-    if (t < ntiles) op.lanes_issue(t, slot_a(k), slot_a(k) + kLaneRegion, lane);
+    if (t < ntiles) op.template lanes_issue<B>(t, slot_a(k), slot_a(k) + TW, lane);
     cp_async_commit_ge();
   }
   for (uint32_t k = 0;; ++k) {
     const uint64_t tile = tile0 + k * gwarps;
     if (tile >= ntiles) break;
-    const uint64_t tn = tile + (kLaneStages - 1) * gwarps;
-    if (tn < ntiles)
-      op.lanes_issue(tn, slot_a(k + kLaneStages - 1), slot_a(k + kLaneStages - 1) + kLaneRegion,
-                     lane);
+    const uint64_t tn = tile + (S - 1) * gwarps;
+    if (tn < ntiles) op.template lanes_issue<B>(tn, slot_a(k + S - 1), slot_a(k + S - 1) + TW, lane);
     cp_async_commit_ge();
-    cp_async_wait2_ge();  // tile k has landed (groups complete in order)
+    if constexpr (S == 3)
+      cp_async_wait2_ge();  // tile k has landed (groups complete in order)
+    else
+      cp_async_wait1_ge();
     __syncwarp();
     const uint32_t* bufa = slot_a(k);
     uint32_t wa[B + 1], wb[B + 1];
     lds_words<B>(bufa, lane * B, wa);
     wa[B] = 0;
     if constexpr (Op::kTwoInputs) {
-      lds_words<B>(bufa + kLaneRegion, lane * B, wb);
+      lds_words<B>(bufa + TW, lane * B, wb);
       wb[B] = 0;
+    }
+    if constexpr (SGN) {
+#pragma unroll
+      for (int i = 0; i < B; ++i) {
+        wa[i] ^= group_sign_bits(B, i);
+        if constexpr (Op::kTwoInputs) wb[i] ^= group_sign_bits(B, i);
+      }
     }
     uint32_t ow[BS + 1];
 #pragma unroll
     for (int i = 0; i <= BS; ++i) ow[i] = 0;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const uint32_t r = op.template lanes4<B>(wa, wb, c);
-      orb |= r;
-      const uint32_t t = compact_c<BS>(r);
-      const int bit = 4 * BS * c, wi = bit >> 5, sh = bit & 31;
+    for (int c = 0; c < 32 / K; ++c) {
+      const uint32_t r = op.template lanes_k<B, L, SGN>(wa, wb, c, orb, neg);
+      const uint32_t t = compact_l<BS, L>(r);
+      const int bit = K * BS * c, wi = bit >> 5, sh = bit & 31;
       ow[wi] |= t << sh;
-      if (sh + 4 * BS > 32) ow[wi + 1] |= t >> (32 - sh);
+      if (sh + K * BS > 32) ow[wi + 1] |= t >> (32 - sh);
     }
     sts_words<BS>(obuf, lane * BS, ow);
     __syncwarp();
@@ -424,51 +519,75 @@ __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t*
     __syncwarp();
   }
   cp_async_wait0_ge();
-  uint32_t o = orb | (orb >> 8) | (orb >> 16) | (orb >> 24);
-  o = __reduce_or_sync(0xffffffffu, o & 0xffu);
-  if (lane == 0 && o) atomicOr(reinterpret_cast<unsigned long long*>(&out->stat_or),
-                               (unsigned long long)o);
+  uint32_t o = orb;
+  if constexpr (L == 8) o = (o | (o >> 8) | (o >> 16) | (o >> 24)) & 0xffu;
+  if constexpr (L == 16) o = (o | (o >> 16)) & 0xffffu;
+  o = __reduce_or_sync(0xffffffffu, o);
+  const uint32_t ng = __reduce_or_sync(0xffffffffu, neg);
+  if (lane == 0) {
+    if (o) atomicOr(reinterpret_cast<unsigned long long*>(&out->stat_or), (unsigned long long)o);
+    if (ng) atomicOr(&out->stat_neg, 1u);
+  }
 }
 
-// Calls lanes_body for the run-time (b, bs): add B <= 7 with BS = B + 1,
-// scale B <= BS <= 8.
+// Calls lanes_body for the run-time (b, bs, sign): add B <= 31 with
+// BS = B + 1 in the smallest lane that holds B + 1 bits; scale (non-negative)
+// B <= BS <= 8 in bytes.
 template <class Op, int B = 1, int BS = 1>
-__device__ __forceinline__ void lanes_dispatch(const Op& op, int b, int bs, ccm_header* out,
-                                               uint32_t* words, uint64_t n, uint32_t* sbuf) {
-  if constexpr (B <= 8) {
+__device__ __forceinline__ void lanes_dispatch(const Op& op, int b, int bs, int sgn,
+                                               ccm_header* out, uint32_t* words, uint64_t n,
+                                               uint32_t* sbuf) {
+  if constexpr (Op::kTwoInputs) {
+    if constexpr (B <= 31) {
+      if (b == B) {
+        constexpr int L = B + 1 <= 8 ? 8 : (B + 1 <= 16 ? 16 : 32);
+        if (sgn)
+          lanes_body<Op, B, B + 1, L, true>(op, out, words, n, sbuf);
+        else
+          lanes_body<Op, B, B + 1, L, false>(op, out, words, n, sbuf);
+        return;
+      }
+      lanes_dispatch<Op, B + 1, B + 2>(op, b, bs, sgn, out, words, n, sbuf);
+    }
+  } else if constexpr (B <= 8) {
     if constexpr (BS > 8) {
-      lanes_dispatch<Op, B + 1, B + 1>(op, b, bs, out, words, n, sbuf);
+      lanes_dispatch<Op, B + 1, B + 1>(op, b, bs, sgn, out, words, n, sbuf);
     } else {
-      constexpr bool valid = Op::kTwoInputs ? (B <= 7 && BS == B + 1) : (BS >= B);
-      if constexpr (valid) {
+      if constexpr (BS >= B) {
         if (b == B && bs == BS) {
-          lanes_body<Op, B, BS>(op, out, words, n, sbuf);
+          lanes_body<Op, B, BS, 8, false>(op, out, words, n, sbuf);
           return;
         }
       }
-      lanes_dispatch<Op, B, BS + 1>(op, b, bs, out, words, n, sbuf);
+      lanes_dispatch<Op, B, BS + 1>(op, b, bs, sgn, out, words, n, sbuf);
     }
   }
 }
 
+// `warp_words`: shared words per warp (lane_warp_words of the host's width
+// bound); the dynamic shared memory is kWarps times that.
 template <class Op>
 __global__ void __launch_bounds__(kThreads) k_ew_lanes(Op op, ccm_header* out, uint32_t* words,
-                                                       uint64_t capacity, uint64_t n) {
-  __shared__ __align__(16) uint32_t s_buf[kWarps][(2 * kLaneStages + 1) * kLaneRegion];
+                                                       uint64_t capacity, uint64_t n,
+                                                       uint32_t warp_words) {
+  extern __shared__ __align__(16) uint32_t s_lanes[];
   if (out->status != CCM_OK) return;
   op.init(n);
   const int bs = op.spec_width();
-  const int B = (bs <= 8 && words_for(n, bs) <= capacity) ? op.lanes_width(bs) : 0;
+  int B = (bs <= 32 && words_for(n, bs) <= capacity) ? op.lanes_width(bs) : 0;
+  if (B && lane_warp_words(B) > warp_words) B = 0;  // (buffers sized for narrower inputs)
   if (!B) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) out->reserved1 = 1;
-  lanes_dispatch<Op>(op, B, bs, out, words, n, s_buf[threadIdx.x / kWarp]);
+  lanes_dispatch<Op>(op, B, bs, op.lanes_sign(), out, words, n,
+                     s_lanes + (threadIdx.x / kWarp) * warp_words);
 }
 
 // Host launchers (ew_lanes.cu).
+// `bmax`: the host's bound on the input width (from the buffer capacities).
 void launch_lanes_add(const OpAdd& op, ccm_header* out, uint32_t* words, uint64_t capacity,
-                      uint64_t n, cudaStream_t st);
+                      uint64_t n, int bmax, cudaStream_t st);
 void launch_lanes_scale(const OpScale<true>& op, ccm_header* out, uint32_t* words,
-                        uint64_t capacity, uint64_t n, cudaStream_t st);
+                        uint64_t capacity, uint64_t n, int bmax, cudaStream_t st);
 
 template <class Op, int BMAX, int MODE>
 __global__ void __launch_bounds__(kThreads) k_ew(Op op, ccm_header* out, uint32_t* words,
@@ -834,7 +953,7 @@ int launch_ew_class(const EwCall& c, cudaStream_t st) {
       if (c.kind == EwKind::AddStats)
         k_ew<OpAdd, C, kStats><<<g, kThreads, 0, st>>>(op, c.out, nullptr, 0, n, 0);
       else if (c.kind == EwKind::AddSpec) {
-        launch_lanes_add(op, c.out, c.words, c.capacity, n, st);
+        launch_lanes_add(op, c.out, c.words, c.capacity, n, C < 31 ? C : 31, st);
         launched = 2;
         k_ew<OpAdd, C, kSpec><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity, n, 0);
       }
@@ -852,7 +971,7 @@ int launch_ew_class(const EwCall& c, cudaStream_t st) {
           k_ew<OpScale<true>, C, kStats><<<g, kThreads, 0, st>>>(op, c.out, nullptr, 0, n, 0);
         else if (c.kind == EwKind::ScaleSpec) {
           if (c.s >= 1 && c.s < 256) {  // (byte lanes need 1 <= s < 2^8)
-            launch_lanes_scale(op, c.out, c.words, c.capacity, n, st);
+            launch_lanes_scale(op, c.out, c.words, c.capacity, n, C < 8 ? C : 8, st);
             launched = 2;
           }
           k_ew<OpScale<true>, C, kSpec><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity,
