@@ -311,8 +311,8 @@ def run_gpu(args, rank, world, local_rank):
         return None
     hbm, peak_kind = peaks()
     kernels = {"pack": "ge::k_pack_local<int64_t, 8>", "unpack": "ge::k_unpack_ge<int64_t, 8>",
-               "add": "ge::k_ew<OpAdd, 8, spec> + finish",
-               "scale": "ge::k_ew<OpScale<true>, 16, spec> + finish",
+               "add": "ge::k_ew_lanes<OpAdd> (+ k_ew spec/finish, which return at once)",
+               "scale": "ge::k_ew_lanes<OpScale<true>> (+ k_ew spec/finish, which return at once)",
                "matvec": "mvf::k_matvec_rows<8, narrow>"}
     per_op = {}
     for k, t in kern_ms.items():

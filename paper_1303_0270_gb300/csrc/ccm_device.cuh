@@ -67,6 +67,18 @@ __device__ __forceinline__ int64_t extend(uint64_t bits, int b, int sgn) {
   return (int64_t)(bits & ((1ull << b) - 1ull));
 }
 
+// Positions of the sign bits of the 32 fields of a B-bit group (B words)
+// that fall in word i of the group: XOR-ing them turns two's complement
+// fields into offset binary (u = a + 2^(B-1)).
+__host__ __device__ constexpr uint32_t group_sign_bits(int B, int i) {
+  uint32_t m = 0;
+  for (int e = 0; e < 32; ++e) {
+    const int p = e * B + B - 1;
+    if ((p >> 5) == i) m |= 1u << (p & 31);
+  }
+  return m;
+}
+
 // Field e of a stream at runtime width b (1..64), straight from global
 // memory.  Touches only words that hold bits of the field.
 __device__ __forceinline__ int64_t decode_field(const uint32_t* __restrict__ w, uint64_t e, int b,

@@ -205,18 +205,6 @@ __device__ __forceinline__ uint32_t compact_l(uint32_t v) {
   }
 }
 
-// Positions of the sign bits of the 32 fields of a B-bit group that fall in
-// word i of the group (the word-level XOR that turns two's complement fields
-// into offset binary, u = a + 2^(B-1)).
-__host__ __device__ constexpr uint32_t group_sign_bits(int B, int i) {
-  uint32_t m = 0;
-  for (int e = 0; e < 32; ++e) {
-    const int p = e * B + B - 1;
-    if ((p >> 5) == i) m |= 1u << (p & 31);
-  }
-  return m;
-}
-
 // NW consecutive shared words from word w0 (w0 a multiple of the vector
 // width chosen: 4 words when NW % 4 == 0, else 2 when even, else 1).
 template <int NW>
@@ -256,7 +244,6 @@ __device__ __forceinline__ void sts_words(uint32_t* buf, int w0, const uint32_t*
   }
 }
 
-
 // ---------------------------------------------------------------------------
 // Operations.  produce() hands every field value of the lane's group to
 // sink(k, value) as Val<BMAX> (int32 when the class bounds every value below
@@ -265,6 +252,25 @@ __device__ __forceinline__ void sts_words(uint32_t* buf, int w0, const uint32_t*
 // zero bits above the last field (a packed matrix is canonical) or from the
 // zero fill of words past the end, and give 0 in every operation.
 // ---------------------------------------------------------------------------
+// Lane results r in offset binary at width BS (r = c + 2^(BS-1), every lane
+// below 2^BS): c >= 0 exactly when bit BS - 1 of the lane is set; returns the
+// two's complement bits of c (r ^ 2^(BS-1)) and ORs the folded values
+// (c >= 0 ? c : ~c, the bits below BS - 1) into `orb`, the sign into `neg`.
+template <int BS, int L>
+__device__ __forceinline__ uint32_t offset_out(uint32_t r, uint32_t& orb, uint32_t& neg) {
+  constexpr uint32_t ones = lane_ones<L>();
+  constexpr uint32_t lo1 = BS - 1 >= 32 ? ~0u : (1u << (BS - 1)) - 1u;
+  constexpr uint32_t lo = lo1 * ones;
+  constexpr uint32_t top = (1u << (BS - 1)) * ones;
+  const uint32_t pos = ((r >> (BS - 1)) & ones) * lo1;  // lanes with c >= 0
+  orb |= (r ^ lo ^ pos) & lo;
+  neg |= ~r & top;
+  return r ^ top;
+}
+
+// Lane size (bits) that holds a BS-bit result.
+__host__ __device__ constexpr int lane_bits(int bs) { return bs <= 8 ? 8 : (bs <= 16 ? 16 : 32); }
+
 struct OpAdd {
   PackedIn a, b;
   template <int BMAX>
@@ -289,27 +295,30 @@ struct OpAdd {
   __device__ __forceinline__ int lanes_width(int bs) const {
     return (a.sgn == b.sgn && a.b == b.b && a.b <= 31 && bs == a.b + 1) ? a.b : 0;
   }
-  __device__ __forceinline__ int lanes_sign() const { return a.sgn; }
+  static constexpr int kLaneGrow = 1;  // BS = B + 1
+  // Lane mode: 0 unsigned operands, 1 signed (offset binary in and out).
+  __device__ __forceinline__ int lanes_mode() const { return a.sgn; }
+  // Mask of the sign-bit XOR on the inputs in mode 1 (all of them here).
+  __device__ __forceinline__ uint32_t lanes_in_xor() const { return ~0u; }
+  struct LaneConst {};
+  template <int B, int BS, int L, int MODE>
+  __device__ __forceinline__ LaneConst lanes_const() const {
+    return {};
+  }
   // Chunk c of the lane's group: the sums, one per lane, as the output
-  // field bits (width B + 1), with the statistics of the result.  Signed
-  // inputs arrive in offset binary (u = a + 2^(B-1)), so s = u_a + u_b =
-  // c + 2^B: c >= 0 exactly when bit B of s is set, the output bits are
-  // s ^ 2^B, and the folded value (c >= 0 ? c : ~c) is s or ~s below bit B.
-  template <int B, int L, bool SGN>
+  // field bits (width BS = B + 1), with the statistics of the result.
+  // Signed inputs arrive in offset binary (u = a + 2^(B-1)), so
+  // u_a + u_b = c + 2^B is the sum in offset binary at width B + 1.
+  template <int B, int BS, int L, int MODE>
   __device__ __forceinline__ uint32_t lanes_k(const uint32_t* wa, const uint32_t* wb, int c,
-                                              uint32_t& orb, uint32_t& neg) const {
+                                              uint32_t& orb, uint32_t& neg,
+                                              const LaneConst&) const {
     const uint32_t sum = spread_l<B, L>(wa, c) + spread_l<B, L>(wb, c);
-    if constexpr (!SGN) {
+    if constexpr (MODE == 0) {
       orb |= sum;
       return sum;
     } else {
-      constexpr uint32_t ones = lane_ones<L>();
-      constexpr uint32_t lo = (B >= 32 ? ~0u : (1u << B) - 1u) * ones;
-      constexpr uint32_t bitb = (1u << B) * ones;
-      const uint32_t pos = ((sum >> B) & ones) * (lo / ones);  // lanes with c >= 0
-      orb |= (sum ^ lo ^ pos) & lo;
-      neg |= ~sum & bitb;
-      return sum ^ bitb;
+      return offset_out<BS, L>(sum, orb, neg);
     }
   }
   static constexpr bool kTwoInputs = true;
@@ -371,18 +380,62 @@ struct OpScale {
     if (lo < -lim || hi >= lim) return 65;
     return range_width((int64_t)lo, (int64_t)hi);
   }
-  // Byte lanes: A non-negative with at most 8 bits, s >= 1, every product
-  // below 2^8 (so the result width is at least A's); returns A's width.
+  // Lanes apply for 1 <= |s| < 2^5, A of at most 31 bits and a speculative
+  // width BS = B + D with 1 <= D <= kLaneGrow and B + bitlen|s| at most the
+  // lane size of BS (so that no lane product carries into the next lane),
+  // except 1-bit signed A with s < 0 (values {-1, 0}: a non-negative result
+  // range, not the signed one mode 1 writes).  Returns B (0: not applicable).
+  static constexpr int kLaneGrow = 4;
   __device__ __forceinline__ int lanes_width(int bs) const {
-    return (!a.sgn && s >= 1 && a.b <= 8 && bs <= 8) ? a.b : 0;
+    const int64_t t = s < 0 ? -s : s;
+    if (t < 1 || t >= 32 || a.b > 31 || bs - a.b < 1 || bs - a.b > kLaneGrow) return 0;
+    if (a.sgn && a.b == 1 && s < 0) return 0;
+    return a.b + bitlen64((uint64_t)t) <= lane_bits(bs) ? a.b : 0;
   }
-  __device__ __forceinline__ int lanes_sign() const { return 0; }
-  template <int B, int L, bool SGN>
+  // Lane mode: 0 unsigned A and s > 0 (unsigned result); 1 signed A, or
+  // unsigned A and s < 0 (offset binary out; the sign-bit XOR on the input
+  // only for signed A).
+  __device__ __forceinline__ int lanes_mode() const { return (a.sgn || s < 0) ? 1 : 0; }
+  __device__ __forceinline__ uint32_t lanes_in_xor() const { return a.sgn ? ~0u : 0u; }
+  // With t = |s| and v = u (s > 0) or its B-bit complement (s < 0), where u
+  // is A's field in offset binary (signed) or plain (unsigned), the result
+  // in offset binary at width BS is r = t v + P for one constant P >= 0:
+  //   signed, s > 0:   c = t u - t 2^(B-1),        P = 2^(BS-1) - t 2^(B-1)
+  //   signed, s < 0:   c = t v - t (2^(B-1) - 1),  P = 2^(BS-1) - t (2^(B-1) - 1)
+  //   unsigned, s < 0: c = t v - t (2^B - 1),      P = 2^(BS-1) - t (2^B - 1)
+  // (mode 0: r = t a, P = 0; mode 1: the other three).  BS is the width of s times A's range, so every
+  // r lies in [0, 2^BS) and every t v below 2^L: one multiply and one add
+  // per register of lanes, no carry between lanes.
+  struct LaneConst {
+    uint32_t t, cmask, p;
+  };
+  template <int B, int BS, int L, int MODE>
+  __device__ __forceinline__ LaneConst lanes_const() const {
+    constexpr uint32_t ones = lane_ones<L>();
+    constexpr uint32_t lob = (1u << B) - 1u;
+    const uint32_t t = (uint32_t)(s < 0 ? -s : s);
+    if constexpr (MODE == 0) {
+      return {t, 0u, 0u};
+    } else {
+      const uint32_t half = 1u << (BS - 1);
+      const uint32_t p = !a.sgn ? half - t * lob
+                         : s > 0 ? half - t * (1u << (B - 1))
+                                 : half - t * ((1u << (B - 1)) - 1u);
+      return {t, s < 0 ? lob * ones : 0u, p * ones};
+    }
+  }
+  template <int B, int BS, int L, int MODE>
   __device__ __forceinline__ uint32_t lanes_k(const uint32_t* wa, const uint32_t*, int c,
-                                              uint32_t& orb, uint32_t&) const {
-    const uint32_t r = spread_l<B, L>(wa, c) * (uint32_t)s;
-    orb |= r;
-    return r;
+                                              uint32_t& orb, uint32_t& neg,
+                                              const LaneConst& kc) const {
+    const uint32_t v = spread_l<B, L>(wa, c);
+    if constexpr (MODE == 0) {
+      const uint32_t r = v * kc.t;
+      orb |= r;
+      return r;
+    } else {
+      return offset_out<BS, L>((v ^ kc.cmask) * kc.t + kc.p, orb, neg);
+    }
   }
   static constexpr bool kTwoInputs = false;
   template <int B>
@@ -432,31 +485,39 @@ constexpr int kStats = 0, kPack = 1, kSpec = 2;
 // those; the warp then writes the output tile with 16-byte stores.
 __host__ __device__ constexpr int lane_stages(int B) { return B <= 8 ? 3 : 2; }
 
-// Shared words per warp for input widths up to bmax (the largest over
-// b <= bmax of the ring and the output tile of width b + 1).
-__host__ __device__ constexpr uint32_t lane_warp_words(int bmax) {
+// Shared words per warp of the pass at input width b and output width bs
+// with `inputs` operands: the ring, then the output tile.
+__host__ __device__ constexpr uint32_t lane_body_words(int b, int bs, int inputs) {
+  return (uint32_t)(lane_stages(b) * inputs * 32 * b + 32 * bs);
+}
+
+// Shared words per warp for input widths up to bmax and output widths up to
+// `grow` bits wider (at most 32).
+__host__ __device__ constexpr uint32_t lane_warp_words(int bmax, int inputs, int grow) {
   uint32_t m = 0;
   for (int b = 1; b <= bmax; ++b) {
-    const uint32_t v = (uint32_t)(lane_stages(b) * 2 * 32 * b + 32 * (b + 1));
+    const uint32_t v = lane_body_words(b, b + grow < 32 ? b + grow : 32, inputs);
     if (v > m) m = v;
   }
   return m;
 }
 
-template <class Op, int B, int BS, int L, bool SGN>
+template <class Op, int B, int BS, int L, int MODE>
 __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t* words,
                                         uint64_t n, uint32_t* sbuf) {
   constexpr int S = lane_stages(B);
   constexpr int TW = 32 * B;  // words of an input tile
+  constexpr int NI = Op::kTwoInputs ? 2 : 1;
   constexpr int K = 32 / L;   // fields per register
+  const typename Op::LaneConst kc = op.template lanes_const<B, BS, L, MODE>();
   const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
   const uint64_t dw = data_words(n, BS);
   const uint64_t ntiles = (n + kTile - 1) / kTile;
   const uint64_t gwarps = (uint64_t)gridDim.x * kWarps;
   const uint64_t tile0 = (uint64_t)blockIdx.x * kWarps + warp;
-  // per warp: S slots of (A tile, B tile), then the output tile
-  uint32_t* obuf = sbuf + S * 2 * TW;
-  auto slot_a = [&](uint32_t k) { return sbuf + (k % S) * 2 * TW; };
+  // per warp: S slots of (A tile[, B tile]), then the output tile
+  uint32_t* obuf = sbuf + S * NI * TW;
+  auto slot_a = [&](uint32_t k) { return sbuf + (k % S) * NI * TW; };
   uint32_t orb = 0, neg = 0;
   // cp.async ring: the next S - 1 tiles in flight while tile k is decoded
 #pragma unroll
@@ -484,11 +545,12 @@ __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t*
       lds_words<B>(bufa + TW, lane * B, wb);
       wb[B] = 0;
     }
-    if constexpr (SGN) {
+    if constexpr (MODE == 1) {  // signed operands: offset binary
+      const uint32_t xs = op.lanes_in_xor();
 #pragma unroll
       for (int i = 0; i < B; ++i) {
-        wa[i] ^= group_sign_bits(B, i);
-        if constexpr (Op::kTwoInputs) wb[i] ^= group_sign_bits(B, i);
+        wa[i] ^= group_sign_bits(B, i) & xs;
+        if constexpr (Op::kTwoInputs) wb[i] ^= group_sign_bits(B, i) & xs;
       }
     }
     uint32_t ow[BS + 1];
@@ -496,7 +558,7 @@ __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t*
     for (int i = 0; i <= BS; ++i) ow[i] = 0;
 #pragma unroll
     for (int c = 0; c < 32 / K; ++c) {
-      const uint32_t r = op.template lanes_k<B, L, SGN>(wa, wb, c, orb, neg);
+      const uint32_t r = op.template lanes_k<B, BS, L, MODE>(wa, wb, c, orb, neg, kc);
       const uint32_t t = compact_l<BS, L>(r);
       const int bit = K * BS * c, wi = bit >> 5, sh = bit & 31;
       ow[wi] |= t << sh;
@@ -530,37 +592,39 @@ __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t*
   }
 }
 
-// Calls lanes_body for the run-time (b, bs, sign): add B <= 31 with
-// BS = B + 1 in the smallest lane that holds B + 1 bits; scale (non-negative)
-// B <= BS <= 8 in bytes.
-template <class Op, int B = 1, int BS = 1>
-__device__ __forceinline__ void lanes_dispatch(const Op& op, int b, int bs, int sgn,
+// Calls lanes_body for the run-time (b, bs, mode).  Add: B <= 31 with
+// BS = B + 1; scale: B <= 31 with BS = B + D, 1 <= D <= kLaneGrow.  The lane
+// size is the smallest of 8, 16, 32 bits that holds BS.
+template <class Op, int B, int BS>
+__device__ __forceinline__ void lanes_modes(const Op& op, int mode, ccm_header* out,
+                                            uint32_t* words, uint64_t n, uint32_t* sbuf) {
+  constexpr int L = lane_bits(BS);
+  if (mode == 0)
+    lanes_body<Op, B, BS, L, 0>(op, out, words, n, sbuf);
+  else
+    lanes_body<Op, B, BS, L, 1>(op, out, words, n, sbuf);
+}
+
+template <class Op, int B, int D = 1>
+__device__ __forceinline__ void lanes_grow(const Op& op, int d, int mode, ccm_header* out,
+                                           uint32_t* words, uint64_t n, uint32_t* sbuf) {
+  if constexpr (B + D <= 32 && D <= Op::kLaneGrow) {
+    if (d == D)
+      lanes_modes<Op, B, B + D>(op, mode, out, words, n, sbuf);
+    else
+      lanes_grow<Op, B, D + 1>(op, d, mode, out, words, n, sbuf);
+  }
+}
+
+template <class Op, int B = 1>
+__device__ __forceinline__ void lanes_dispatch(const Op& op, int b, int bs, int mode,
                                                ccm_header* out, uint32_t* words, uint64_t n,
                                                uint32_t* sbuf) {
-  if constexpr (Op::kTwoInputs) {
-    if constexpr (B <= 31) {
-      if (b == B) {
-        constexpr int L = B + 1 <= 8 ? 8 : (B + 1 <= 16 ? 16 : 32);
-        if (sgn)
-          lanes_body<Op, B, B + 1, L, true>(op, out, words, n, sbuf);
-        else
-          lanes_body<Op, B, B + 1, L, false>(op, out, words, n, sbuf);
-        return;
-      }
-      lanes_dispatch<Op, B + 1, B + 2>(op, b, bs, sgn, out, words, n, sbuf);
-    }
-  } else if constexpr (B <= 8) {
-    if constexpr (BS > 8) {
-      lanes_dispatch<Op, B + 1, B + 1>(op, b, bs, sgn, out, words, n, sbuf);
-    } else {
-      if constexpr (BS >= B) {
-        if (b == B && bs == BS) {
-          lanes_body<Op, B, BS, 8, false>(op, out, words, n, sbuf);
-          return;
-        }
-      }
-      lanes_dispatch<Op, B, BS + 1>(op, b, bs, sgn, out, words, n, sbuf);
-    }
+  if constexpr (B <= 31) {
+    if (b == B)
+      lanes_grow<Op, B>(op, bs - B, mode, out, words, n, sbuf);
+    else
+      lanes_dispatch<Op, B + 1>(op, b, bs, mode, out, words, n, sbuf);
   }
 }
 
@@ -575,10 +639,11 @@ __global__ void __launch_bounds__(kThreads) k_ew_lanes(Op op, ccm_header* out, u
   op.init(n);
   const int bs = op.spec_width();
   int B = (bs <= 32 && words_for(n, bs) <= capacity) ? op.lanes_width(bs) : 0;
-  if (B && lane_warp_words(B) > warp_words) B = 0;  // (buffers sized for narrower inputs)
+  if (B && lane_body_words(B, bs, Op::kTwoInputs ? 2 : 1) > warp_words)
+    B = 0;  // (buffers sized for narrower inputs)
   if (!B) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) out->reserved1 = 1;
-  lanes_dispatch<Op>(op, B, bs, op.lanes_sign(), out, words, n,
+  lanes_dispatch<Op>(op, B, bs, op.lanes_mode(), out, words, n,
                      s_lanes + (threadIdx.x / kWarp) * warp_words);
 }
 
@@ -660,7 +725,6 @@ __global__ void __launch_bounds__(kThreads) k_ew(Op op, ccm_header* out, uint32_
     }
   }
 }
-
 
 // Pack pass of a dense int32/int64 matrix (its statistics come from k_stats).
 template <typename T, int BMAX>
@@ -929,14 +993,59 @@ inline int ew_grid(uint64_t n, int per_sm) {
   return (int)umin(umax(want, 1), (uint64_t)num_sms() * per_sm);
 }
 
-// Returns the number of kernels launched.
+// Launchers of one width class C, one per family of EwKind (each family is
+// instantiated in a translation unit of its own so that they compile in
+// parallel).  Each returns the number of kernels launched.  Grids are
+// persistent-style: every warp keeps walking tiles (and prefetching).
+
+// AddStats / AddSpec / AddPack
 template <int C>
-int launch_ew_class(const EwCall& c, cudaStream_t st) {
+int launch_ew_add(const EwCall& c, cudaStream_t st) {
   int launched = 1;
   const uint64_t n = c.rows * c.cols;
   PackedIn a{c.ha, c.wa, 0, 0, 0}, b{c.hb, c.wb, 0, 0, 0};
-  // Persistent-style grids: every warp keeps walking tiles (and prefetching).
   const int g = ew_grid(n, 8);
+  const OpAdd op{a, b};
+  if (c.kind == EwKind::AddStats)
+    k_ew<OpAdd, C, kStats><<<g, kThreads, 0, st>>>(op, c.out, nullptr, 0, n, 0);
+  else if (c.kind == EwKind::AddSpec) {
+    launch_lanes_add(op, c.out, c.words, c.capacity, n, C < 31 ? C : 31, st);
+    launched = 2;
+    k_ew<OpAdd, C, kSpec><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity, n, 0);
+  } else
+    k_ew<OpAdd, C, kPack><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity, n, c.spec);
+  return launched;
+}
+
+// ScaleStats / ScaleSpec / ScalePack; SMALL: |s| < 2^15 (OpScale<SMALL>)
+template <int C, bool SMALL>
+int launch_ew_scale(const EwCall& c, cudaStream_t st) {
+  int launched = 1;
+  const uint64_t n = c.rows * c.cols;
+  const OpScale<SMALL> op{PackedIn{c.ha, c.wa, 0, 0, 0}, c.s};
+  const int g = ew_grid(n, 8);
+  if (c.kind == EwKind::ScaleStats) {
+    k_ew<OpScale<SMALL>, C, kStats><<<g, kThreads, 0, st>>>(op, c.out, nullptr, 0, n, 0);
+  } else if (c.kind == EwKind::ScaleSpec) {
+    if constexpr (SMALL) {
+      if (c.s != 0 && c.s > -32 && c.s < 32) {  // (the lane pass needs 1 <= |s| < 2^5)
+        launch_lanes_scale(op, c.out, c.words, c.capacity, n, C < 31 ? C : 31, st);
+        launched = 2;
+      }
+    }
+    k_ew<OpScale<SMALL>, C, kSpec><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity, n,
+                                                           0);
+  } else {
+    k_ew<OpScale<SMALL>, C, kPack><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity, n,
+                                                           c.spec);
+  }
+  return launched;
+}
+
+// PackI64 / PackI32 / LocalI64 / LocalI32 / Repack / UnpackI64 / UnpackI32
+template <int C>
+int launch_ew_pack(const EwCall& c, cudaStream_t st) {
+  const uint64_t n = c.rows * c.cols;
   switch (c.kind) {
     case EwKind::PackI64:
       k_pack_dense<int64_t, C><<<ew_grid(n, 12), kThreads, 0, st>>>(
@@ -946,53 +1055,6 @@ int launch_ew_class(const EwCall& c, cudaStream_t st) {
       k_pack_dense<int32_t, C><<<ew_grid(n, 12), kThreads, 0, st>>>(
           (const int32_t*)c.dense, c.out, c.words, c.capacity, n);
       break;
-    case EwKind::AddStats:
-    case EwKind::AddSpec:
-    case EwKind::AddPack: {
-      const OpAdd op{a, b};
-      if (c.kind == EwKind::AddStats)
-        k_ew<OpAdd, C, kStats><<<g, kThreads, 0, st>>>(op, c.out, nullptr, 0, n, 0);
-      else if (c.kind == EwKind::AddSpec) {
-        launch_lanes_add(op, c.out, c.words, c.capacity, n, C < 31 ? C : 31, st);
-        launched = 2;
-        k_ew<OpAdd, C, kSpec><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity, n, 0);
-      }
-      else
-        k_ew<OpAdd, C, kPack><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity, n, c.spec);
-      break;
-    }
-    case EwKind::ScaleStats:
-    case EwKind::ScaleSpec:
-    case EwKind::ScalePack: {
-      const bool small = c.s > -32768 && c.s < 32768;
-      if (small) {
-        const OpScale<true> op{a, c.s};
-        if (c.kind == EwKind::ScaleStats)
-          k_ew<OpScale<true>, C, kStats><<<g, kThreads, 0, st>>>(op, c.out, nullptr, 0, n, 0);
-        else if (c.kind == EwKind::ScaleSpec) {
-          if (c.s >= 1 && c.s < 256) {  // (byte lanes need 1 <= s < 2^8)
-            launch_lanes_scale(op, c.out, c.words, c.capacity, n, C < 8 ? C : 8, st);
-            launched = 2;
-          }
-          k_ew<OpScale<true>, C, kSpec><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity,
-                                                                n, 0);
-        }
-        else
-          k_ew<OpScale<true>, C, kPack><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity,
-                                                                n, c.spec);
-      } else {
-        const OpScale<false> op{a, c.s};
-        if (c.kind == EwKind::ScaleStats)
-          k_ew<OpScale<false>, C, kStats><<<g, kThreads, 0, st>>>(op, c.out, nullptr, 0, n, 0);
-        else if (c.kind == EwKind::ScaleSpec)
-          k_ew<OpScale<false>, C, kSpec><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity,
-                                                                 n, 0);
-        else
-          k_ew<OpScale<false>, C, kPack><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity,
-                                                                 n, c.spec);
-      }
-      break;
-    }
     case EwKind::LocalI64:
     case EwKind::LocalI32:
     case EwKind::Repack: {
@@ -1030,8 +1092,38 @@ int launch_ew_class(const EwCall& c, cudaStream_t st) {
       k_unpack_ge<int32_t, C><<<ew_grid(n, 12), kThreads, 0, st>>>(
           c.out, c.words, c.rows, c.cols, c.capacity, (int32_t*)c.dense, c.err);
       break;
+    default:
+      return 0;
   }
-  return launched;
+  return 1;
+}
+
+extern template int launch_ew_add<8>(const EwCall&, cudaStream_t);
+extern template int launch_ew_add<16>(const EwCall&, cudaStream_t);
+extern template int launch_ew_add<32>(const EwCall&, cudaStream_t);
+extern template int launch_ew_scale<8, true>(const EwCall&, cudaStream_t);
+extern template int launch_ew_scale<16, true>(const EwCall&, cudaStream_t);
+extern template int launch_ew_scale<32, true>(const EwCall&, cudaStream_t);
+extern template int launch_ew_scale<8, false>(const EwCall&, cudaStream_t);
+extern template int launch_ew_scale<16, false>(const EwCall&, cudaStream_t);
+extern template int launch_ew_scale<32, false>(const EwCall&, cudaStream_t);
+extern template int launch_ew_pack<8>(const EwCall&, cudaStream_t);
+extern template int launch_ew_pack<16>(const EwCall&, cudaStream_t);
+extern template int launch_ew_pack<32>(const EwCall&, cudaStream_t);
+
+template <int C>
+inline int launch_ew_class(const EwCall& c, cudaStream_t st) {
+  switch (c.kind) {
+    case EwKind::AddStats:
+    case EwKind::AddSpec:
+    case EwKind::AddPack: return launch_ew_add<C>(c, st);
+    case EwKind::ScaleStats:
+    case EwKind::ScaleSpec:
+    case EwKind::ScalePack:
+      return c.s > -32768 && c.s < 32768 ? launch_ew_scale<C, true>(c, st)
+                                         : launch_ew_scale<C, false>(c, st);
+    default: return launch_ew_pack<C>(c, st);
+  }
 }
 
 }  // namespace ge

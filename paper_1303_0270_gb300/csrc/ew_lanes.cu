@@ -1,43 +1,14 @@
-// ew_lanes.cu -- the lane pass of add and scale (see ew_kernels.cuh),
-// instantiated once here rather than in every width-class unit.
-#include "ew_kernels.cuh"
+// ew_lanes.cu -- the lane pass of add (see ew_kernels.cuh), instantiated
+// once here rather than in every width-class unit; scale's lane pass is in
+// ew_lanes_scale.cu.
+#include "ew_lanes.cuh"
 
 namespace ccm {
 namespace ge {
 
-// One wave: the tiles are assigned to warps statically (grid stride), so a
-// second wave of CTAs would only add a tail.  Shared memory per CTA from the
-// width bound.
-template <class Op>
-static void launch_lanes(const Op& op, ccm_header* out, uint32_t* words, uint64_t capacity,
-                         uint64_t n, int bmax, cudaStream_t st) {
-  const uint32_t ww = lane_warp_words(bmax);
-  const size_t smem = (size_t)kWarps * ww * sizeof(uint32_t);
-  static int dev_done = -1;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev_done != dev) {
-    int optin = 0;
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncSetAttribute(k_ew_lanes<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    dev_done = dev;
-  }
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ew_lanes<Op>, kThreads, smem) !=
-          cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
-  k_ew_lanes<Op><<<ew_grid(n, per_sm), kThreads, smem, st>>>(op, out, words, capacity, n, ww);
-}
-
 void launch_lanes_add(const OpAdd& op, ccm_header* out, uint32_t* words, uint64_t capacity,
                       uint64_t n, int bmax, cudaStream_t st) {
   launch_lanes<OpAdd>(op, out, words, capacity, n, bmax, st);
-}
-
-void launch_lanes_scale(const OpScale<true>& op, ccm_header* out, uint32_t* words,
-                        uint64_t capacity, uint64_t n, int bmax, cudaStream_t st) {
-  launch_lanes<OpScale<true>>(op, out, words, capacity, n, bmax, st);
 }
 
 }  // namespace ge

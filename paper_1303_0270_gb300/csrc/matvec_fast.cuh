@@ -181,17 +181,6 @@ __device__ __forceinline__ void decode_mac(const uint8_t* row, const int* __rest
   if constexpr (NARROW) acc += acc32;
 }
 
-// Positions of the sign bits of the 32 fields of a group (b words) that
-// fall in word i of the group.
-__host__ __device__ constexpr uint32_t sign_bits(int B, int i) {
-  uint32_t m = 0;
-  for (int e = 0; e < 32; ++e) {
-    const int p = e * B + B - 1;
-    if ((p >> 5) == i) m |= 1u << (p & 31);
-  }
-  return m;
-}
-
 __host__ __device__ constexpr uint32_t low_bits(int n) { return n >= 32 ? ~0u : (1u << n) - 1u; }
 
 // Widths whose fields never straddle a byte: a word splits into 8/b
@@ -242,7 +231,7 @@ __device__ __forceinline__ int dp4a_stage(const uint8_t* row, const int* __restr
   w[4 * B] = 0;
   if constexpr (SGN) {
 #pragma unroll
-    for (int i = 0; i < 4 * B; ++i) w[i] ^= sign_bits(B, i % B);
+    for (int i = 0; i < 4 * B; ++i) w[i] ^= group_sign_bits(B, i % B);
   }
   const int4* xv = reinterpret_cast<const int4*>(xw);
   int acc[4] = {0, 0, 0, 0};  // four independent dp4a chains

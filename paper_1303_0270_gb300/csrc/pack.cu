@@ -8,12 +8,6 @@
 
 namespace ccm {
 
-namespace ge {
-extern template int launch_ew_class<8>(const EwCall& c, cudaStream_t st);
-extern template int launch_ew_class<16>(const EwCall& c, cudaStream_t st);
-extern template int launch_ew_class<32>(const EwCall& c, cudaStream_t st);
-}  // namespace ge
-
 int width_bound(uint64_t capacity, uint64_t n) {
   if (n == 0) return 64;
   return (int)umin(capacity * 32 / n, 64);

@@ -330,6 +330,58 @@ def test_scale_speculative_width(ccm, b, sgn, s):
                            f"scale spec b={b} s={sgn} by {s} top={top}")
 
 
+def _range_width(lo, hi):
+    """Eq. 1 width of the values [lo, hi] (two's complement when lo < 0)."""
+    h = max(hi, 0).bit_length()
+    return max(h, 1) if lo >= 0 else 1 + max(h, (~lo).bit_length())
+
+
+def _scale_lanes_expected(b, sgn, s, bs):
+    """Whether the scale lane pass applies: 1 <= |s| < 32, A of at most 31
+    bits, 1 <= bs - b <= 4, b + bitlen|s| at most the lane size of bs, and
+    not 1-bit signed A with s < 0."""
+    t = abs(s)
+    lane = 8 if bs <= 8 else (16 if bs <= 16 else 32)
+    return 1 <= t < 32 and b <= 31 and 1 <= bs - b <= 4 and bs <= 32 and \
+        b + t.bit_length() <= lane and not (sgn and b == 1 and s < 0)
+
+
+@pytest.mark.parametrize("b,sgn", [(1, 0), (1, 1), (3, 0), (5, 0), (7, 1), (8, 1), (12, 1),
+                                   (13, 0), (16, 1), (20, 1), (27, 1), (28, 0), (29, 1), (31, 1)])
+@pytest.mark.parametrize("s", [2, -1, -2, 3, 7, -7, 8, -8, 15, -16, 31, -31])
+def test_scale_lanes(ccm, b, sgn, s):
+    """Scale through the lane pass (offset binary for signed A or negative s),
+    output capacity at the speculative width so that the width class allows
+    it: word-identical to the oracle with the range extremes present (one
+    pass) and absent (the exact width is smaller: second pass), and the lane
+    pass ran exactly where its conditions hold."""
+    shape = (5, 3001)
+    lo, hi = synth.signed_range(b) if sgn else (0, (1 << b) - 1)
+    bs = _range_width(*sorted((s * lo, s * hi)))
+    a = _rand(b * 5 + sgn + 3 * abs(s), shape, b, bool(sgn))
+    for top in (True, False):
+        v = a.copy()
+        if top:
+            v.flat[0], v.flat[-1] = lo, hi
+        else:
+            v = np.clip(v, lo // 2 if sgn else 0, hi // 2)
+        oa = oracle.pack(v)
+        expect = oracle.scale(oa, s)
+        pa = ccm.pack(to_dev(v), capacity=ccm.words_for(*shape, b))
+        out = ccm.PackedMatrix(*shape, ccm.words_for(*shape, min(bs, 64)), device())
+        ccm.scale_into(pa, s, out)
+        assert_same_packed(out, expect, f"scale lanes b={b} sgn={sgn} by {s} top={top}")
+        # the speculative width follows A's packed width and sign
+        alo, ahi = synth.signed_range(oa.width) if oa.is_signed else (0, (1 << oa.width) - 1)
+        spec = _range_width(*sorted((s * alo, s * ahi)))
+        n = shape[0] * shape[1]
+        cls_ok = max(min(m.capacity * 32 // n, 64) for m in (pa, out)) <= 32  # width class
+        lanes = cls_ok and \
+            _scale_lanes_expected(oa.width, oa.is_signed, s, spec)
+        assert out.header().reserved1 == int(lanes), \
+            f"lane pass use b={oa.width} sgn={oa.is_signed} s={s} spec={spec}"
+
+
 @pytest.mark.parametrize("m,n", [(1, 128), (31, 256), (300, 384), (257, 1280), (1000, 128)])
 @pytest.mark.parametrize("ba,bx,sa", [(1, 1, 0), (3, 8, 1), (5, 8, 0), (8, 8, 1), (12, 7, 1),
                                       (16, 8, 0), (17, 8, 1), (24, 16, 1), (31, 8, 0), (32, 8, 1),
