@@ -253,7 +253,9 @@ ccm_status ccm_gen_poisson(int64_t* out, uint64_t count, uint64_t seed, uint64_t
  *
  * ccm_batch_matvec launches an initialisation kernel (validates the headers,
  * clears y headers and the scratch) and the persistent kernel (`grid` CTAs;
- * <= 0 picks 3 per SM).  `ws` is device workspace of at least
+ * <= 0 picks 3 per SM).  Its shared memory holds x of max_cols entries and
+ * each warp's two staging slots for A widths up to info->max_width (an info
+ * with max_width outside 1..32 or max_cols above 8192: CCM_E_INVAL).  `ws` is device workspace of at least
  * ccm_batch_workspace_bytes(...) bytes, 256-byte aligned.  Each y_i header
  * receives its own status.  Both launches are stream-ordered and can be
  * captured in a CUDA graph. */
@@ -270,6 +272,8 @@ typedef struct ccm_batch_info {
   uint32_t unit_segments; /* segments per unit */
   uint32_t max_cols;      /* widest entry (sizes the kernel's shared memory) */
   uint64_t plan_bytes;
+  uint32_t max_width;     /* widest A the capacities admit, <= 32 (sizes the staging) */
+  uint32_t reserved;
 } ccm_batch_info;
 
 size_t ccm_batch_plan_bytes(const ccm_batch_entry* entries, int count, uint32_t unit_segments);

@@ -3,10 +3,14 @@
 //
 // Work unit: a run of consecutive 32-field row segments of one matrix.  Row i
 // of an m x n matrix is cut into ceil(n / 32) segments of up to 32 fields; a
-// lane owns one segment.  A segment starts at an arbitrary bit, so the lane
-// loads the b + 1 words that cover it, funnel-shifts them once to the
-// segment's start and then decodes its fields with shifts fixed at compile
-// time (the width is dispatched per unit on the GPU).  x is decoded once per
+// lane owns one segment.  A warp takes 32 consecutive segments at a time (a
+// chunk: one contiguous word range) and streams its chunks through a
+// two-slot cp.async ring in shared memory, so the words of the next chunk are
+// in flight while the current one is decoded.  A segment starts at an
+// arbitrary bit, so the lane reads the b + 1 words that cover it,
+// funnel-shifts them once to the segment's start and then decodes its fields
+// with shifts fixed at compile time (the width is dispatched per unit on the
+// GPU).  x is decoded once per
 // unit into shared memory in a [f/4][segment][f%4] layout, so the four x
 // values a lane needs next are one conflict-free 16-byte load.  Lanes of a
 // warp hold consecutive segments; a segmented shuffle reduction keyed by row
@@ -31,7 +35,13 @@ namespace bt {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxCols = 8192;      // x of at most 8192 entries per matrix (32 KB of shared)
-constexpr int kWordsPerWarp = 32 * 32 + 64;  // staging for 32 segments of width <= 32
+
+// Shared words of one ring slot for A widths up to bmax: a chunk covers at
+// most 32 * 32 fields, i.e. 32 bmax + 2 words (the lanes read one word past
+// their segment), plus one padding word per 32 (stage_pos).
+__host__ __device__ constexpr uint32_t slot_words(int bmax) {
+  return (uint32_t)((33 * bmax + 4 + 3) & ~3);
+}
 
 struct Mat {
   const ccm_header* ha;
@@ -44,8 +54,30 @@ struct Mat {
   uint32_t m, n;
   uint64_t y_off;      // offset of this matrix's rows in the int64 y scratch
   uint32_t units;      // work units of this matrix
+  uint32_t nseg_row;   // segments per row, ceil(n / 32)
+  uint32_t dm, ds1, ds2;  // v / nseg_row as a multiply and shifts (DivSeg)
   uint32_t pad;
 };
+
+// Unsigned 32-bit division by a run-time invariant d >= 1 with one high
+// multiply, after Granlund and Montgomery, "Division by invariant integers
+// using multiplication" (1994), Fig. 4.1: with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, q = (t + ((v - t) >> min(l, 1))) >>
+// max(l - 1, 0) where t = mulhi(m, v), for every 32-bit v.
+struct DivSeg {
+  uint32_t m, s1, s2;
+  static DivSeg make(uint32_t d) {
+    int l = 0;
+    while (l < 32 && (1ull << l) < d) ++l;
+    const uint64_t m = (((1ull << l) - d) << 32) / d + 1;
+    return {(uint32_t)m, (uint32_t)(l < 1 ? l : 1), (uint32_t)(l > 1 ? l - 1 : 0)};
+  }
+};
+
+__device__ __forceinline__ uint32_t div_seg(const Mat& M, uint32_t v) {
+  const uint32_t t = __umulhi(v, M.dm);
+  return (t + ((v - t) >> M.ds1)) >> M.ds2;
+}
 
 struct Unit {
   uint32_t mat;
@@ -61,9 +93,53 @@ struct Args {
   int64_t* yscratch;
   uint32_t* ticket;     // unit dispenser
   uint32_t* done;       // per-matrix completed units
+  uint32_t x_ints;      // shared ints of the x region (a multiple of 4)
+  uint32_t slot;        // shared words of one ring slot (slot_words(bmax))
+  uint32_t bmax;        // widest A the slots hold
 };
 
 __device__ __forceinline__ int stage_pos(int w, int b) { return (b & 1) ? w : w + (w >> 5); }
+
+__device__ __forceinline__ void cp_async4(uint32_t* smem, const uint32_t* gmem, uint32_t bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// The word range of the warp's chunk starting at segment `base` of unit u.
+struct Chunk {
+  uint64_t w_first;  // first word (holds the first segment's first bit)
+  uint32_t nwords;   // words through the one after the last segment's last bit
+};
+
+template <int B>
+__device__ __forceinline__ Chunk chunk_of(const Mat& M, const Unit& u, uint32_t base) {
+  const uint32_t n = M.n, nsr = M.nseg_row;
+  const uint32_t first_id = u.seg0 + base;
+  const uint32_t frow = div_seg(M, first_id), fs = first_id - frow * nsr;
+  const uint64_t w_first = (((uint64_t)frow * n + 32 * fs) * B) >> 5;
+  const uint32_t last = min(base + 32, u.nseg) - 1 + u.seg0;
+  const uint32_t lrow = div_seg(M, last), ls = last - lrow * nsr;
+  const uint64_t end_bit = ((uint64_t)lrow * n + min(n, 32 * ls + 32)) * B;
+  return {w_first, (uint32_t)(((end_bit + 31) >> 5) - w_first) + 1};
+}
+
+// cp.async of a chunk's words into a slot (words past the matrix's data
+// words are zero-filled).
+template <int B>
+__device__ __forceinline__ void issue_chunk(const uint32_t* __restrict__ wa, uint64_t dw, Chunk c,
+                                            uint32_t* slot, int lane) {
+  for (uint32_t w = lane; w < c.nwords; w += 32) {
+    const uint64_t g = c.w_first + w;
+    const bool in = g < dw;
+    cp_async4(slot + stage_pos((int)w, B), wa + (in ? g : 0), in ? 4u : 0u);
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Initialisation: validate inputs, write y headers, clear counters and the
@@ -78,7 +154,7 @@ __global__ void k_batch_init(Args a, uint64_t yrows) {
     int st = check_input(M.ha, M.m, M.n, M.a_cap);
     if (st == CCM_OK) st = check_input(M.hx, M.n, 1, M.x_cap);
     // widths the kernel handles, and sums that provably fit int64
-    if (st == CCM_OK && (M.ha->width > 32 || M.hx->width > 31 ||
+    if (st == CCM_OK && (M.ha->width > (int)a.bmax || M.hx->width > 31 ||
                          M.ha->width + M.hx->width + bitlen64(M.n) > 63))
       st = CCM_E_WIDTH;
     ccm_header* y = M.hy;
@@ -101,73 +177,77 @@ __global__ void k_batch_init(Args a, uint64_t yrows) {
 // ---------------------------------------------------------------------------
 template <int B, bool SGN>
 __device__ __noinline__ void run_unit(const Mat& M, const Unit& u, const int4* __restrict__ x4,
-                                      uint32_t nseg_row, uint32_t* stage, int64_t* ys) {
+                                      uint32_t* stage, uint32_t slot_w, int64_t* ys) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const uint32_t n = M.n;
-  for (uint32_t base = warp * 32; base < u.nseg; base += kWarps * 32) {
-    // the warp's 32 consecutive segments
+  const uint32_t n = M.n, nsr = M.nseg_row;
+  const uint64_t dw = data_words((uint64_t)M.m * n, B);
+  uint32_t* slots[2] = {stage, stage + slot_w};
+  uint32_t base = warp * 32;
+  uint64_t w_first = 0;  // of chunk k (the one decoded next)
+  if (base < u.nseg) {
+    const Chunk c = chunk_of<B>(M, u, base);
+    w_first = c.w_first;
+    issue_chunk<B>(M.wa, dw, c, slots[0], lane);
+  }
+  cp_async_commit();
+  for (uint32_t k = 0; base < u.nseg; base += kWarps * 32, ++k) {
+    // the next chunk's words in flight while this one is decoded
+    const uint32_t nb = base + kWarps * 32;
+    uint64_t w_next = 0;
+    if (nb < u.nseg) {
+      const Chunk c = chunk_of<B>(M, u, nb);
+      w_next = c.w_first;
+      issue_chunk<B>(M.wa, dw, c, slots[(k + 1) & 1], lane);
+    }
+    cp_async_commit();
+    cp_async_wait<1>();  // chunk k has landed (groups complete in order)
+    __syncwarp();
+    const uint32_t* sg = slots[k & 1];
+    // the warp's 32 consecutive segments; lane -> (row, segment in the row)
     const uint32_t id = u.seg0 + base + lane;
     const bool live = base + lane < u.nseg;
-    const uint32_t row = live ? id / nseg_row : 0xffffffffu;
-    const uint32_t s = live ? id % nseg_row : 0;
-    const uint32_t col0 = 32 * s;
-    const uint32_t nf = live ? min(32u, n - col0) : 0;
-    const uint64_t bit = ((uint64_t)row * n + col0) * B;
-    // words of all 32 segments: from the first segment's first word
-    const uint32_t first_id = u.seg0 + base;
-    const uint32_t frow = first_id / nseg_row, fs = first_id % nseg_row;
-    const uint64_t w_first = (((uint64_t)frow * n + 32 * fs) * B) >> 5;
-    const uint32_t last = min(base + 32, u.nseg) - 1 + u.seg0;
-    const uint32_t lrow = last / nseg_row, ls = last % nseg_row;
-    const uint64_t end_bit = ((uint64_t)lrow * n + min(n, 32 * ls + 32)) * B;
-    const uint32_t nwords = (uint32_t)(((end_bit + 31) >> 5) - w_first) + 1;
-    const uint64_t dw = data_words((uint64_t)M.m * n, B);
-    // the chunk's words, 8 loads in flight per lane before any is stored
-    for (uint32_t w0 = 0; w0 < nwords; w0 += 8 * 32) {
-      uint32_t tmp[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const uint32_t w = w0 + lane + 32 * j;
-        const uint64_t g = w_first + w;
-        tmp[j] = (w < nwords && g < dw) ? __ldg(M.wa + g) : 0u;
-      }
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const uint32_t w = w0 + lane + 32 * j;
-        if (w < nwords) stage[stage_pos((int)w, B)] = tmp[j];
-      }
-    }
-    __syncwarp();
+    const uint32_t q = div_seg(M, id);
+    const uint32_t row = live ? q : 0xffffffffu;
+    const uint32_t s = live ? id - q * nsr : 0;
+    const uint64_t bit = ((uint64_t)q * n + 32 * s) * B;
     long long acc = 0;
     if (live) {
       const int wo = (int)((bit >> 5) - w_first), s0 = (int)(bit & 31);
       uint32_t w[B + 1];
 #pragma unroll
-      for (int j = 0; j <= B; ++j) w[j] = stage[stage_pos(wo + j, B)];
+      for (int j = 0; j <= B; ++j) w[j] = sg[stage_pos(wo + j, B)];
 #pragma unroll
       for (int j = 0; j < B; ++j) w[j] = __funnelshift_r(w[j], w[j + 1], s0);
       const int4* xv = x4 + s;  // [f/4][segment] of int4
+      // Fields past the row's end meet x = 0 (x is zero-padded to whole
+      // segments), so no per-field bound is needed.
 #pragma unroll
       for (int f4 = 0; f4 < 8; ++f4) {
-        const int4 xq = xv[f4 * nseg_row];
+        const int4 xq = xv[f4 * nsr];
         const int xa[4] = {xq.x, xq.y, xq.z, xq.w};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int f = 4 * f4 + q;
+        for (int qq = 0; qq < 4; ++qq) {
+          const int f = 4 * f4 + qq;
           const int b0 = f * B, wi = b0 >> 5, sh = b0 & 31;
-          uint32_t t = (sh + B <= 32) ? (w[wi] >> sh) : __funnelshift_r(w[wi], w[wi + 1], sh);
-          long long v;
-          if constexpr (B == 32)
-            v = SGN ? (long long)(int)t : (long long)t;
-          else if constexpr (SGN)
-            v = (int)(t << (32 - B)) >> (32 - B);
-          else
-            v = t & ((1u << B) - 1u);
-          if (f < (int)nf) acc += v * xa[q];
+          const uint32_t t =
+              (sh + B <= 32) ? (w[wi] >> sh) : __funnelshift_r(w[wi], w[wi + 1], sh);
+          if constexpr (B == 32 && !SGN) {
+            acc += (long long)t * xa[qq];
+          } else {
+            int v;  // the field as a 32-bit integer
+            if constexpr (B == 32)
+              v = (int)t;
+            else if constexpr (SGN)
+              v = (int)(t << (32 - B)) >> (32 - B);
+            else
+              v = (int)(t & ((1u << B) - 1u));
+            acc += (long long)v * (long long)xa[qq];  // 32 x 32 -> 64 multiply-add
+          }
         }
       }
     }
-    __syncwarp();
+    __syncwarp();  // slot k & 1 is refilled by the issue of chunk k + 2
+    w_first = w_next;
     // segmented reduction by row: the first lane of each row gets the total
     uint32_t r = row;
 #pragma unroll
@@ -180,6 +260,7 @@ __device__ __noinline__ void run_unit(const Mat& M, const Unit& u, const int4* _
     if (live && (lane == 0 || rprev != r))
       atomicAdd(reinterpret_cast<unsigned long long*>(ys + row), (unsigned long long)acc);
   }
+  cp_async_wait<0>();
 }
 
 // Re-pack y of one matrix (m <= 2^31 values in scratch) at its exact width;
@@ -237,9 +318,9 @@ __device__ void pack_y(const Mat& M, const int64_t* __restrict__ ys, uint64_t* s
   }
 }
 
+// Dynamic shared memory: x (a.x_ints ints), then each warp's two ring slots.
 __global__ void __launch_bounds__(kThreads) k_batch_mv(Args a) {
-  extern __shared__ __align__(16) int4 s_x4[];  // kMaxCols ints
-  __shared__ uint32_t s_stage[kWarps][kWordsPerWarp];
+  extern __shared__ __align__(16) int4 s_x4[];
   __shared__ uint32_t s_unit;
   __shared__ int s_last;
   __shared__ uint64_t s_or[kWarps];
@@ -253,7 +334,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_mv(Args a) {
     const Unit u = a.units[ui];
     const Mat& M = a.mats[u.mat];
     const bool ok = M.hy->status == CCM_OK;  // validated by k_batch_init
-    const uint32_t nseg_row = (M.n + 31) / 32;
+    const uint32_t nseg_row = M.nseg_row;
     if (ok) {
       if (cached != u.mat) {
         // x -> shared, layout [f/4][segment][f%4]
@@ -269,11 +350,12 @@ __global__ void __launch_bounds__(kThreads) k_batch_mv(Args a) {
       __syncthreads();
       const int b = M.ha->width, sgn = M.ha->is_signed;
       int64_t* ys = a.yscratch + M.y_off;
-      uint32_t* stage = s_stage[threadIdx.x / 32];
+      uint32_t* stage = reinterpret_cast<uint32_t*>(s_x4) + a.x_ints +
+                        (threadIdx.x / 32) * 2 * a.slot;
       switch (2 * b + sgn) {
-#define CCM_BT_CASE(B)                                                     \
-  case 2 * B: run_unit<B, false>(M, u, s_x4, nseg_row, stage, ys); break; \
-  case 2 * B + 1: run_unit<B, true>(M, u, s_x4, nseg_row, stage, ys); break;
+#define CCM_BT_CASE(B)                                                              \
+  case 2 * B: run_unit<B, false>(M, u, s_x4, stage, a.slot, ys); break; \
+  case 2 * B + 1: run_unit<B, true>(M, u, s_x4, stage, a.slot, ys); break;
         CCM_BT_CASE(1) CCM_BT_CASE(2) CCM_BT_CASE(3) CCM_BT_CASE(4) CCM_BT_CASE(5)
         CCM_BT_CASE(6) CCM_BT_CASE(7) CCM_BT_CASE(8) CCM_BT_CASE(9) CCM_BT_CASE(10)
         CCM_BT_CASE(11) CCM_BT_CASE(12) CCM_BT_CASE(13) CCM_BT_CASE(14) CCM_BT_CASE(15)
@@ -393,6 +475,11 @@ ccm_status ccm_batch_plan(const ccm_batch_entry* entries, int count, uint32_t un
     M.y_cap = e.y.capacity;
     M.m = (uint32_t)e.a.rows;
     M.n = (uint32_t)e.a.cols;
+    M.nseg_row = (uint32_t)((e.a.cols + 31) / 32);
+    const DivSeg dv = DivSeg::make(M.nseg_row ? M.nseg_row : 1);
+    M.dm = dv.m;
+    M.ds1 = dv.s1;
+    M.ds2 = dv.s2;
     M.y_off = yoff;
     yoff += e.a.rows;
     const uint64_t s = segments_of(e);
@@ -404,10 +491,17 @@ ccm_status ccm_batch_plan(const ccm_batch_entry* entries, int count, uint32_t un
       units[u].nseg = (uint32_t)(s ? ccm::umin(unit_segments, s - k * unit_segments) : 0);
     }
   }
-  uint64_t maxcols = 0;
-  for (int i = 0; i < count; ++i) maxcols = ccm::umax(maxcols, entries[i].a.cols);
+  uint64_t maxcols = 0, maxw = 1;
+  for (int i = 0; i < count; ++i) {
+    maxcols = ccm::umax(maxcols, entries[i].a.cols);
+    // the widest A the capacity admits (a valid header's width is at most this)
+    const uint64_t n = entries[i].a.rows * entries[i].a.cols;
+    if (n) maxw = ccm::umax(maxw, ccm::umin(entries[i].a.capacity * 32 / n, 32));
+  }
   info->count = (uint32_t)count;
   info->max_cols = (uint32_t)maxcols;
+  info->max_width = (uint32_t)maxw;
+  info->reserved = 0;
   info->units = L.nunits;
   info->y_rows = L.yrows;
   info->unit_segments = unit_segments;
@@ -436,21 +530,28 @@ ccm_status ccm_batch_matvec(const void* plan, const ccm_batch_info* info, void* 
   a.yscratch = (int64_t*)ws;
   a.done = (uint32_t*)((uint8_t*)ws + align256(info->y_rows * 8));
   a.ticket = (uint32_t*)((uint8_t*)ws + align256(info->y_rows * 8) + align256((size_t)info->count * 4));
+  // x of the widest entry (rounded to whole 32-field segments), then the
+  // warps' ring slots sized for the widest A
+  if (info->max_width < 1 || info->max_width > 32 || info->max_cols > (uint32_t)kMaxCols)
+    return CCM_E_INVAL;
+  a.x_ints = (info->max_cols + 31) / 32 * 32;
+  a.slot = slot_words((int)info->max_width);
+  a.bmax = info->max_width;
+  const size_t smem = (size_t)(a.x_ints + kWarps * 2 * a.slot) * sizeof(uint32_t);
+  if (grid <= 0) grid = ccm::num_sms() * 3;
+  static size_t attr = 0;
+  if (smem > attr) {
+    if (cudaFuncSetAttribute(k_batch_mv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return CCM_E_CUDA;
+    attr = smem;
+  }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const uint64_t init_items = ccm::umax(info->y_rows, info->count);
   int gi = (int)ccm::umin((init_items + 255) / 256, (uint64_t)ccm::num_sms() * 8);
   k_batch_init<<<gi < 1 ? 1 : gi, 256, 0, st>>>(a, info->y_rows);
-  // x of the widest entry in shared memory (rounded to whole 32-field segments)
-  const size_t xbytes = (size_t)((info->max_cols + 31) / 32 * 32) * sizeof(int) + 16;
-  if (grid <= 0) grid = ccm::num_sms() * 3;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_batch_mv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kMaxCols * (int)sizeof(int) + 16);
-    attr = true;
-  }
   ccm::profile_begin(st);
-  k_batch_mv<<<grid, kThreads, xbytes, st>>>(a);
+  k_batch_mv<<<grid, kThreads, smem, st>>>(a);
   ccm::profile_end(st);
   ccm::note_launch(2);
   return cudaGetLastError() == cudaSuccess ? CCM_OK : CCM_E_CUDA;

@@ -119,3 +119,31 @@ def test_batch_errors(ccm):
     assert bm.ys[0].status == ccm.E_WIDTH
     assert np.array_equal(ccm.unpack(bm.ys[1].check()).cpu().numpy().ravel(),
                           ccm.unpack(a).cpu().numpy() @ np.ones(4, dtype=np.int64))
+
+
+def test_batch_wide_widths_and_loose_capacity(ccm):
+    """Widths 25..32 (the staging slots sized for the widest A the capacities
+    admit) and entries packed into buffers much larger than their width needs
+    (bound clamped at 32): every y against the oracle."""
+    from paper_1303_0270_gb300.batch import BatchMatvec
+    mats, xs, pa = [], [], []
+    shapes = [(33, 70), (7, 2048), (130, 33), (64, 64), (1, 500), (257, 96)]
+    for k, (r, c) in enumerate(shapes):
+        for b in (25, 28, 31, 32, 3):
+            a = synth.uniform_signed(1000 + 7 * k + b, synth.STREAM_A, r * c, b).reshape(r, c)
+            if (k + b) % 2:
+                a = np.abs(a) if b < 32 else a
+            x = synth.uniform_signed(2000 + k + b, synth.STREAM_X, c, 8).reshape(-1, 1)
+            mats.append(a)
+            xs.append(x)
+            loose = (k + b) % 3 == 0
+            pa.append(ccm.pack(to_dev(a), capacity=ccm.words_for(r, c, 64)) if loose
+                      else _pack_exact(ccm, a))
+    px = [_pack_exact(ccm, x) for x in xs]
+    for us in (32, 512):
+        bm = BatchMatvec(pa, px, unit_segments=us)
+        bm.launch()
+        torch.cuda.synchronize()
+        for i, (a, x) in enumerate(zip(mats, xs)):
+            o = oracle.matvec(oracle.pack(a), oracle.pack(x))
+            assert_same_packed(bm.ys[i], o, f"wide batch entry {i} {a.shape} us={us}")
