@@ -253,9 +253,11 @@ ccm_status ccm_gen_poisson(int64_t* out, uint64_t count, uint64_t seed, uint64_t
  *
  * ccm_batch_matvec launches an initialisation kernel (validates the headers,
  * clears y headers and the scratch) and the persistent kernel (`grid` CTAs;
- * <= 0 picks 3 per SM).  Its shared memory holds x of max_cols entries and
- * each warp's two staging slots for A widths up to info->max_width (an info
- * with max_width outside 1..32 or max_cols above 8192: CCM_E_INVAL).  `ws` is device workspace of at least
+ * <= 0 picks 3 per SM).  The initialisation kernel (one block per entry)
+ * also decodes every x into an int32 image in `ws`; the main kernel's shared
+ * memory holds each warp's two staging slots for A widths up to
+ * info->max_width (an info with max_width outside 1..32 or max_cols above
+ * 8192: CCM_E_INVAL).  `ws` is device workspace of at least
  * ccm_batch_workspace_bytes(...) bytes, 256-byte aligned.  Each y_i header
  * receives its own status.  Both launches are stream-ordered and can be
  * captured in a CUDA graph. */
@@ -274,6 +276,7 @@ typedef struct ccm_batch_info {
   uint64_t plan_bytes;
   uint32_t max_width;     /* widest A the capacities admit, <= 32 (sizes the staging) */
   uint32_t reserved;
+  uint64_t x_ints;        /* ints of the decoded-x images in the workspace */
 } ccm_batch_info;
 
 size_t ccm_batch_plan_bytes(const ccm_batch_entry* entries, int count, uint32_t unit_segments);

@@ -10,9 +10,10 @@
 // arbitrary bit, so the lane reads the b + 1 words that cover it,
 // funnel-shifts them once to the segment's start and then decodes its fields
 // with shifts fixed at compile time (the width is dispatched per unit on the
-// GPU).  x is decoded once per
-// unit into shared memory in a [f/4][segment][f%4] layout, so the four x
-// values a lane needs next are one conflict-free 16-byte load.  Lanes of a
+// GPU).  Every x is decoded once, by the initialisation kernel, into an int32
+// image in workspace with the [f/4][segment][f%4] layout (zero past the row's
+// end), so the four x values a lane needs next are one 16-byte load
+// (L1-resident while a matrix's units run).  Lanes of a
 // warp hold consecutive segments; a segmented shuffle reduction keyed by row
 // leaves each row's partial sum in its first lane, which adds it to the int64
 // y scratch with one atomic.
@@ -54,6 +55,7 @@ struct Mat {
   uint32_t m, n;
   uint64_t y_off;      // offset of this matrix's rows in the int64 y scratch
   uint32_t units;      // work units of this matrix
+  uint64_t x_off;      // offset of this matrix's x image (ints; a multiple of 32)
   uint32_t nseg_row;   // segments per row, ceil(n / 32)
   uint32_t dm, ds1, ds2;  // v / nseg_row as a multiply and shifts (DivSeg)
   uint32_t pad;
@@ -93,7 +95,7 @@ struct Args {
   int64_t* yscratch;
   uint32_t* ticket;     // unit dispenser
   uint32_t* done;       // per-matrix completed units
-  uint32_t x_ints;      // shared ints of the x region (a multiple of 4)
+  int* ximage;          // decoded x of every matrix (Mat::x_off)
   uint32_t slot;        // shared words of one ring slot (slot_words(bmax))
   uint32_t bmax;        // widest A the slots hold
 };
@@ -145,12 +147,11 @@ __device__ __forceinline__ void issue_chunk(const uint32_t* __restrict__ wa, uin
 // Initialisation: validate inputs, write y headers, clear counters and the
 // y scratch.
 // ---------------------------------------------------------------------------
-__global__ void k_batch_init(Args a, uint64_t yrows) {
-  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = tid; i < yrows; i += stride) a.yscratch[i] = 0;
-  for (uint64_t i = tid; i < a.nmats; i += stride) {
-    const Mat& M = a.mats[i];
+__global__ void k_batch_init(Args a) {
+  __shared__ int s_st;
+  const uint32_t i = blockIdx.x;  // one block per matrix
+  const Mat& M = a.mats[i];
+  if (threadIdx.x == 0) {
     int st = check_input(M.ha, M.m, M.n, M.a_cap);
     if (st == CCM_OK) st = check_input(M.hx, M.n, 1, M.x_cap);
     // widths the kernel handles, and sums that provably fit int64
@@ -168,8 +169,20 @@ __global__ void k_batch_init(Args a, uint64_t yrows) {
     y->stat_or = 0;
     y->stat_neg = 0;
     a.done[i] = 0;
+    if (i == 0) *a.ticket = 0;
+    s_st = st;
   }
-  if (tid == 0) *a.ticket = 0;
+  for (uint32_t r = threadIdx.x; r < M.m; r += blockDim.x) a.yscratch[M.y_off + r] = 0;
+  __syncthreads();
+  if (s_st != CCM_OK) return;
+  // x -> image, layout [f/4][segment][f%4], zero past n
+  const int bx = M.hx->width, sx = M.hx->is_signed;
+  const uint32_t nsr = M.nseg_row;
+  int* xi = a.ximage + M.x_off;
+  for (uint32_t j = threadIdx.x; j < nsr * 32; j += blockDim.x) {
+    const uint32_t seg = j / 32, f = j % 32;
+    xi[((f / 4) * nsr + seg) * 4 + (f % 4)] = j < M.n ? (int)decode_field(M.wx, j, bx, sx) : 0;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -218,12 +231,12 @@ __device__ __noinline__ void run_unit(const Mat& M, const Unit& u, const int4* _
       for (int j = 0; j <= B; ++j) w[j] = sg[stage_pos(wo + j, B)];
 #pragma unroll
       for (int j = 0; j < B; ++j) w[j] = __funnelshift_r(w[j], w[j + 1], s0);
-      const int4* xv = x4 + s;  // [f/4][segment] of int4
+      const int4* xv = x4 + s;  // [f/4][segment] of int4 (the matrix's image)
       // Fields past the row's end meet x = 0 (x is zero-padded to whole
       // segments), so no per-field bound is needed.
 #pragma unroll
       for (int f4 = 0; f4 < 8; ++f4) {
-        const int4 xq = xv[f4 * nsr];
+        const int4 xq = __ldg(xv + f4 * nsr);
         const int xa[4] = {xq.x, xq.y, xq.z, xq.w};
 #pragma unroll
         for (int qq = 0; qq < 4; ++qq) {
@@ -318,14 +331,13 @@ __device__ void pack_y(const Mat& M, const int64_t* __restrict__ ys, uint64_t* s
   }
 }
 
-// Dynamic shared memory: x (a.x_ints ints), then each warp's two ring slots.
+// Dynamic shared memory: each warp's two ring slots.
 __global__ void __launch_bounds__(kThreads) k_batch_mv(Args a) {
-  extern __shared__ __align__(16) int4 s_x4[];
+  extern __shared__ __align__(16) uint32_t s_slots[];
   __shared__ uint32_t s_unit;
   __shared__ int s_last;
   __shared__ uint64_t s_or[kWarps];
   __shared__ uint32_t s_neg[kWarps];
-  uint32_t cached = 0xffffffffu;  // matrix whose x is in shared memory
   for (;;) {
     if (threadIdx.x == 0) s_unit = atomicAdd(a.ticket, 1u);
     __syncthreads();
@@ -334,28 +346,15 @@ __global__ void __launch_bounds__(kThreads) k_batch_mv(Args a) {
     const Unit u = a.units[ui];
     const Mat& M = a.mats[u.mat];
     const bool ok = M.hy->status == CCM_OK;  // validated by k_batch_init
-    const uint32_t nseg_row = M.nseg_row;
     if (ok) {
-      if (cached != u.mat) {
-        // x -> shared, layout [f/4][segment][f%4]
-        const int bx = M.hx->width, sx = M.hx->is_signed;
-        int* xs = reinterpret_cast<int*>(s_x4);
-        for (uint32_t j = threadIdx.x; j < nseg_row * 32; j += blockDim.x) {
-          const uint32_t seg = j / 32, f = j % 32;
-          const int v = j < M.n ? (int)decode_field(M.wx, j, bx, sx) : 0;
-          xs[((f / 4) * nseg_row + seg) * 4 + (f % 4)] = v;
-        }
-        cached = u.mat;
-      }
-      __syncthreads();
       const int b = M.ha->width, sgn = M.ha->is_signed;
       int64_t* ys = a.yscratch + M.y_off;
-      uint32_t* stage = reinterpret_cast<uint32_t*>(s_x4) + a.x_ints +
-                        (threadIdx.x / 32) * 2 * a.slot;
+      uint32_t* stage = s_slots + (threadIdx.x / 32) * 2 * a.slot;
+      const int4* x4 = reinterpret_cast<const int4*>(a.ximage + M.x_off);
       switch (2 * b + sgn) {
 #define CCM_BT_CASE(B)                                                              \
-  case 2 * B: run_unit<B, false>(M, u, s_x4, stage, a.slot, ys); break; \
-  case 2 * B + 1: run_unit<B, true>(M, u, s_x4, stage, a.slot, ys); break;
+  case 2 * B: run_unit<B, false>(M, u, x4, stage, a.slot, ys); break; \
+  case 2 * B + 1: run_unit<B, true>(M, u, x4, stage, a.slot, ys); break;
         CCM_BT_CASE(1) CCM_BT_CASE(2) CCM_BT_CASE(3) CCM_BT_CASE(4) CCM_BT_CASE(5)
         CCM_BT_CASE(6) CCM_BT_CASE(7) CCM_BT_CASE(8) CCM_BT_CASE(9) CCM_BT_CASE(10)
         CCM_BT_CASE(11) CCM_BT_CASE(12) CCM_BT_CASE(13) CCM_BT_CASE(14) CCM_BT_CASE(15)
@@ -390,6 +389,19 @@ namespace ccm {
 namespace bt {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// x image of an n-column matrix: whole 32-field segments.
+uint64_t x_image_ints(uint64_t cols) { return (cols + 31) / 32 * 32; }
+
+// Workspace: int64 y scratch, per-matrix done counters, the ticket, x images.
+size_t ws_done(uint64_t yrows) { return align256(yrows * 8); }
+size_t ws_ticket(uint64_t yrows, uint32_t count) {
+  return ws_done(yrows) + align256((size_t)count * 4);
+}
+size_t ws_ximage(uint64_t yrows, uint32_t count) { return ws_ticket(yrows, count) + 256; }
+size_t ws_bytes(uint64_t yrows, uint32_t count, uint64_t xints) {
+  return ws_ximage(yrows, count) + align256(xints * 4);
+}
 
 struct Layout {
   uint32_t nmats = 0, nunits = 0;
@@ -441,9 +453,12 @@ size_t ccm_batch_plan_bytes(const ccm_batch_entry* entries, int count, uint32_t 
 
 size_t ccm_batch_workspace_bytes(const ccm_batch_entry* entries, int count) {
   if (!entries || count <= 0) return 0;
-  uint64_t yrows = 0;
-  for (int i = 0; i < count; ++i) yrows += entries[i].a.rows;
-  return ccm::bt::align256(yrows * 8) + ccm::bt::align256((size_t)count * 4) + 256;
+  uint64_t yrows = 0, xints = 0;
+  for (int i = 0; i < count; ++i) {
+    yrows += entries[i].a.rows;
+    xints += ccm::bt::x_image_ints(entries[i].a.cols);
+  }
+  return ccm::bt::ws_bytes(yrows, (uint32_t)count, xints);
 }
 
 ccm_status ccm_batch_plan(const ccm_batch_entry* entries, int count, uint32_t unit_segments,
@@ -460,7 +475,7 @@ ccm_status ccm_batch_plan(const ccm_batch_entry* entries, int count, uint32_t un
   std::vector<uint8_t> host(L.bytes, 0);
   Mat* mats = reinterpret_cast<Mat*>(host.data() + L.mats_off);
   Unit* units = reinterpret_cast<Unit*>(host.data() + L.units_off);
-  uint64_t yoff = 0, u = 0;
+  uint64_t yoff = 0, xoff = 0, u = 0;
   for (int i = 0; i < count; ++i) {
     const ccm_batch_entry& e = entries[i];
     Mat& M = mats[i];
@@ -482,6 +497,8 @@ ccm_status ccm_batch_plan(const ccm_batch_entry* entries, int count, uint32_t un
     M.ds2 = dv.s2;
     M.y_off = yoff;
     yoff += e.a.rows;
+    M.x_off = xoff;
+    xoff += x_image_ints(e.a.cols);
     const uint64_t s = segments_of(e);
     const uint64_t nu = s ? (s + unit_segments - 1) / unit_segments : 1;
     M.units = (uint32_t)nu;
@@ -502,6 +519,7 @@ ccm_status ccm_batch_plan(const ccm_batch_entry* entries, int count, uint32_t un
   info->max_cols = (uint32_t)maxcols;
   info->max_width = (uint32_t)maxw;
   info->reserved = 0;
+  info->x_ints = xoff;
   info->units = L.nunits;
   info->y_rows = L.yrows;
   info->unit_segments = unit_segments;
@@ -517,8 +535,8 @@ ccm_status ccm_batch_matvec(const void* plan, const ccm_batch_info* info, void* 
   using namespace ccm::bt;
   if (!plan || !info || !ws || info->count == 0) return CCM_E_INVAL;
   if (reinterpret_cast<uintptr_t>(ws) % 256) return CCM_E_INVAL;
-  const size_t need = align256(info->y_rows * 8) + align256((size_t)info->count * 4) + 256;
-  if (ws_bytes < need) return CCM_E_CAPACITY;
+  if (ws_bytes < ccm::bt::ws_bytes(info->y_rows, info->count, info->x_ints))
+    return CCM_E_CAPACITY;
   Layout L;
   L.mats_off = align256(sizeof(ccm_batch_info));
   L.units_off = L.mats_off + align256(sizeof(Mat) * (size_t)info->count);
@@ -528,16 +546,15 @@ ccm_status ccm_batch_matvec(const void* plan, const ccm_batch_info* info, void* 
   a.nmats = info->count;
   a.nunits = info->units;
   a.yscratch = (int64_t*)ws;
-  a.done = (uint32_t*)((uint8_t*)ws + align256(info->y_rows * 8));
-  a.ticket = (uint32_t*)((uint8_t*)ws + align256(info->y_rows * 8) + align256((size_t)info->count * 4));
-  // x of the widest entry (rounded to whole 32-field segments), then the
-  // warps' ring slots sized for the widest A
+  a.done = (uint32_t*)((uint8_t*)ws + ws_done(info->y_rows));
+  a.ticket = (uint32_t*)((uint8_t*)ws + ws_ticket(info->y_rows, info->count));
+  a.ximage = (int*)((uint8_t*)ws + ws_ximage(info->y_rows, info->count));
+  // the warps' ring slots, sized for the widest A
   if (info->max_width < 1 || info->max_width > 32 || info->max_cols > (uint32_t)kMaxCols)
     return CCM_E_INVAL;
-  a.x_ints = (info->max_cols + 31) / 32 * 32;
   a.slot = slot_words((int)info->max_width);
   a.bmax = info->max_width;
-  const size_t smem = (size_t)(a.x_ints + kWarps * 2 * a.slot) * sizeof(uint32_t);
+  const size_t smem = (size_t)kWarps * 2 * a.slot * sizeof(uint32_t);
   if (grid <= 0) grid = ccm::num_sms() * 3;
   static size_t attr = 0;
   if (smem > attr) {
@@ -547,9 +564,7 @@ ccm_status ccm_batch_matvec(const void* plan, const ccm_batch_info* info, void* 
     attr = smem;
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const uint64_t init_items = ccm::umax(info->y_rows, info->count);
-  int gi = (int)ccm::umin((init_items + 255) / 256, (uint64_t)ccm::num_sms() * 8);
-  k_batch_init<<<gi < 1 ? 1 : gi, 256, 0, st>>>(a, info->y_rows);
+  k_batch_init<<<info->count, 256, 0, st>>>(a);
   ccm::profile_begin(st);
   k_batch_mv<<<grid, kThreads, smem, st>>>(a);
   ccm::profile_end(st);
