@@ -147,3 +147,20 @@ def test_batch_wide_widths_and_loose_capacity(ccm):
         for i, (a, x) in enumerate(zip(mats, xs)):
             o = oracle.matvec(oracle.pack(a), oracle.pack(x))
             assert_same_packed(bm.ys[i], o, f"wide batch entry {i} {a.shape} us={us}")
+
+
+@pytest.mark.parametrize("whi", [12, 16, 20, 24])
+def test_batch_bounded_widths(ccm, whi):
+    """Batches of widths up to 12, 16, 20, 24 (shapes of at least 16 x 16, so
+    the capacity bound is the width itself and the staging slots are sized to
+    it): every y against the oracle."""
+    from paper_1303_0270_gb300.batch import BatchMatvec
+    mats, xs = _batch_inputs(80 + whi, 40, lo=16, hi=400, wlo=1, whi=whi)
+    pa = [_pack_exact(ccm, a) for a in mats]
+    px = [_pack_exact(ccm, x) for x in xs]
+    bm = BatchMatvec(pa, px, unit_segments=128)
+    bm.launch()
+    torch.cuda.synchronize()
+    for i, (a, x) in enumerate(zip(mats, xs)):
+        assert_same_packed(bm.ys[i], oracle.matvec(oracle.pack(a), oracle.pack(x)),
+                           f"class batch whi={whi} entry {i} {a.shape}")
