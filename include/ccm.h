@@ -89,8 +89,9 @@ typedef struct ccm_header {
   uint64_t nwords;    /* ccm_words_for(rows, cols, width) */
   uint64_t stat_or;   /* internal: OR over the result of (a >= 0 ? a : ~a) */
   uint32_t stat_neg;  /* internal: 1 when some entry of the result is negative */
-  uint32_t reserved0;  /* internal (VLB: the largest entry bit length) */
-  uint64_t reserved1;  /* internal (1: an add/scale was written by its byte-lane pass) */
+  uint32_t reserved0;  /* internal (VLB: the largest entry bit length; add/scale written
+                          by the lane pass: the width that pass wrote) */
+  uint64_t reserved1;  /* internal (1: an add/scale was written by its lane pass) */
 } ccm_header;
 
 /* Host-side handle of one packed matrix: where it lives and its shape.

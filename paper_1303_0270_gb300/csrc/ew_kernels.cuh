@@ -268,8 +268,32 @@ __device__ __forceinline__ uint32_t offset_out(uint32_t r, uint32_t& orb, uint32
   return r ^ top;
 }
 
-// Lane size (bits) that holds a BS-bit result.
-__host__ __device__ constexpr int lane_bits(int bs) { return bs <= 8 ? 8 : (bs <= 16 ? 16 : 32); }
+// Lane size (bits) that holds a BS-bit result: 8, 16 or 32 bits (4, 2 or 1
+// fields per 32-bit register), or 64 (one field per 64-bit value) for the
+// results of 33..36 bits.
+__host__ __device__ constexpr int lane_bits(int bs) {
+  return bs <= 8 ? 8 : (bs <= 16 ? 16 : (bs <= 32 ? 32 : 64));
+}
+template <int L>
+using LaneWord = typename std::conditional<(L == 64), uint64_t, uint32_t>::type;
+
+// Field c (B <= 32 bits) of a lane's group, zero-extended to 64 bits.
+template <int B>
+__device__ __forceinline__ uint64_t spread64(const uint32_t* w, int c) {
+  const int bit = B * c, wi = bit >> 5, sh = bit & 31;
+  const uint32_t x = sh + B <= 32 ? (w[wi] >> sh) : __funnelshift_r(w[wi], w[wi + 1], sh);
+  return (uint64_t)(B >= 32 ? x : (x & ((1u << B) - 1u)));
+}
+
+// offset_out for a 64-bit lane (BS = 33..36).
+template <int BS>
+__device__ __forceinline__ uint64_t offset_out64(uint64_t r, uint64_t& orb, uint32_t& neg) {
+  constexpr uint64_t lo = (1ull << (BS - 1)) - 1ull, top = 1ull << (BS - 1);
+  const uint64_t pos = (r >> (BS - 1)) & 1ull;  // c >= 0
+  orb |= (r ^ lo ^ (pos * lo)) & lo;
+  neg |= (uint32_t)(pos ^ 1ull);
+  return r ^ top;
+}
 
 struct OpAdd {
   PackedIn a, b;
@@ -293,7 +317,7 @@ struct OpAdd {
   // mode: the sum then needs B + 1 bits (the speculative width) and fits a
   // lane of 8, 16 or 32 bits.  Returns B (0: not applicable).
   __device__ __forceinline__ int lanes_width(int bs) const {
-    return (a.sgn == b.sgn && a.b == b.b && a.b <= 31 && bs == a.b + 1) ? a.b : 0;
+    return (a.sgn == b.sgn && a.b == b.b && a.b <= 32 && bs == a.b + 1) ? a.b : 0;
   }
   static constexpr int kLaneGrow = 1;  // BS = B + 1
   // Lane mode: 0 unsigned operands, 1 signed (offset binary in and out).
@@ -310,15 +334,25 @@ struct OpAdd {
   // Signed inputs arrive in offset binary (u = a + 2^(B-1)), so
   // u_a + u_b = c + 2^B is the sum in offset binary at width B + 1.
   template <int B, int BS, int L, int MODE>
-  __device__ __forceinline__ uint32_t lanes_k(const uint32_t* wa, const uint32_t* wb, int c,
-                                              uint32_t& orb, uint32_t& neg,
-                                              const LaneConst&) const {
-    const uint32_t sum = spread_l<B, L>(wa, c) + spread_l<B, L>(wb, c);
-    if constexpr (MODE == 0) {
-      orb |= sum;
-      return sum;
+  __device__ __forceinline__ LaneWord<L> lanes_k(const uint32_t* wa, const uint32_t* wb, int c,
+                                                 LaneWord<L>& orb, uint32_t& neg,
+                                                 const LaneConst&) const {
+    if constexpr (L == 64) {
+      const uint64_t sum = spread64<B>(wa, c) + spread64<B>(wb, c);
+      if constexpr (MODE == 0) {
+        orb |= sum;
+        return sum;
+      } else {
+        return offset_out64<BS>(sum, orb, neg);
+      }
     } else {
-      return offset_out<BS, L>(sum, orb, neg);
+      const uint32_t sum = spread_l<B, L>(wa, c) + spread_l<B, L>(wb, c);
+      if constexpr (MODE == 0) {
+        orb |= sum;
+        return sum;
+      } else {
+        return offset_out<BS, L>(sum, orb, neg);
+      }
     }
   }
   static constexpr bool kTwoInputs = true;
@@ -388,7 +422,7 @@ struct OpScale {
   static constexpr int kLaneGrow = 4;
   __device__ __forceinline__ int lanes_width(int bs) const {
     const int64_t t = s < 0 ? -s : s;
-    if (t < 1 || t >= 32 || a.b > 31 || bs - a.b < 1 || bs - a.b > kLaneGrow) return 0;
+    if (t < 1 || t >= 32 || a.b > 32 || bs - a.b < 1 || bs - a.b > kLaneGrow) return 0;
     if (a.sgn && a.b == 1 && s < 0) return 0;
     return a.b + bitlen64((uint64_t)t) <= lane_bits(bs) ? a.b : 0;
   }
@@ -407,34 +441,46 @@ struct OpScale {
   // r lies in [0, 2^BS) and every t v below 2^L: one multiply and one add
   // per register of lanes, no carry between lanes.
   struct LaneConst {
-    uint32_t t, cmask, p;
+    uint32_t t, cmask;  // |s|; the complement mask per register (s < 0)
+    uint64_t p;         // P per register (per 64-bit value when L = 64)
   };
   template <int B, int BS, int L, int MODE>
   __device__ __forceinline__ LaneConst lanes_const() const {
-    constexpr uint32_t ones = lane_ones<L>();
-    constexpr uint32_t lob = (1u << B) - 1u;
+    constexpr uint32_t ones = L == 64 ? 1u : lane_ones<L>();
+    constexpr uint64_t lob = (1ull << B) - 1ull;
     const uint32_t t = (uint32_t)(s < 0 ? -s : s);
     if constexpr (MODE == 0) {
-      return {t, 0u, 0u};
+      return {t, 0u, 0ull};
     } else {
-      const uint32_t half = 1u << (BS - 1);
-      const uint32_t p = !a.sgn ? half - t * lob
-                         : s > 0 ? half - t * (1u << (B - 1))
-                                 : half - t * ((1u << (B - 1)) - 1u);
-      return {t, s < 0 ? lob * ones : 0u, p * ones};
+      const uint64_t half = 1ull << (BS - 1);
+      const uint64_t p = !a.sgn ? half - t * lob
+                         : s > 0 ? half - t * (1ull << (B - 1))
+                                 : half - t * ((1ull << (B - 1)) - 1ull);
+      return {t, s < 0 ? (uint32_t)lob * ones : 0u, p * ones};
     }
   }
   template <int B, int BS, int L, int MODE>
-  __device__ __forceinline__ uint32_t lanes_k(const uint32_t* wa, const uint32_t*, int c,
-                                              uint32_t& orb, uint32_t& neg,
-                                              const LaneConst& kc) const {
-    const uint32_t v = spread_l<B, L>(wa, c);
-    if constexpr (MODE == 0) {
-      const uint32_t r = v * kc.t;
-      orb |= r;
-      return r;
+  __device__ __forceinline__ LaneWord<L> lanes_k(const uint32_t* wa, const uint32_t*, int c,
+                                                 LaneWord<L>& orb, uint32_t& neg,
+                                                 const LaneConst& kc) const {
+    if constexpr (L == 64) {
+      const uint64_t v = spread64<B>(wa, c);
+      if constexpr (MODE == 0) {
+        const uint64_t r = v * kc.t;
+        orb |= r;
+        return r;
+      } else {
+        return offset_out64<BS>((v ^ kc.cmask) * kc.t + kc.p, orb, neg);
+      }
     } else {
-      return offset_out<BS, L>((v ^ kc.cmask) * kc.t + kc.p, orb, neg);
+      const uint32_t v = spread_l<B, L>(wa, c);
+      if constexpr (MODE == 0) {
+        const uint32_t r = v * kc.t;
+        orb |= r;
+        return r;
+      } else {
+        return offset_out<BS, L>((v ^ kc.cmask) * kc.t + (uint32_t)kc.p, orb, neg);
+      }
     }
   }
   static constexpr bool kTwoInputs = false;
@@ -492,11 +538,11 @@ __host__ __device__ constexpr uint32_t lane_body_words(int b, int bs, int inputs
 }
 
 // Shared words per warp for input widths up to bmax and output widths up to
-// `grow` bits wider (at most 32).
+// `grow` bits wider.
 __host__ __device__ constexpr uint32_t lane_warp_words(int bmax, int inputs, int grow) {
   uint32_t m = 0;
   for (int b = 1; b <= bmax; ++b) {
-    const uint32_t v = lane_body_words(b, b + grow < 32 ? b + grow : 32, inputs);
+    const uint32_t v = lane_body_words(b, b + grow, inputs);
     if (v > m) m = v;
   }
   return m;
@@ -508,7 +554,7 @@ __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t*
   constexpr int S = lane_stages(B);
   constexpr int TW = 32 * B;  // words of an input tile
   constexpr int NI = Op::kTwoInputs ? 2 : 1;
-  constexpr int K = 32 / L;   // fields per register
+  constexpr int K = L == 64 ? 1 : 32 / L;  // fields per register (per 64-bit value)
   const typename Op::LaneConst kc = op.template lanes_const<B, BS, L, MODE>();
   const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
   const uint64_t dw = data_words(n, BS);
@@ -518,7 +564,8 @@ __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t*
   // per warp: S slots of (A tile[, B tile]), then the output tile
   uint32_t* obuf = sbuf + S * NI * TW;
   auto slot_a = [&](uint32_t k) { return sbuf + (k % S) * NI * TW; };
-  uint32_t orb = 0, neg = 0;
+  LaneWord<L> orb = 0;
+  uint32_t neg = 0;
   // cp.async ring: the next S - 1 tiles in flight while tile k is decoded
 #pragma unroll
   for (uint32_t k = 0; k < S - 1; ++k) {
@@ -558,11 +605,17 @@ __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t*
     for (int i = 0; i <= BS; ++i) ow[i] = 0;
 #pragma unroll
     for (int c = 0; c < 32 / K; ++c) {
-      const uint32_t r = op.template lanes_k<B, BS, L, MODE>(wa, wb, c, orb, neg, kc);
-      const uint32_t t = compact_l<BS, L>(r);
+      const LaneWord<L> r = op.template lanes_k<B, BS, L, MODE>(wa, wb, c, orb, neg, kc);
       const int bit = K * BS * c, wi = bit >> 5, sh = bit & 31;
-      ow[wi] |= t << sh;
-      if (sh + K * BS > 32) ow[wi + 1] |= t >> (32 - sh);
+      if constexpr (L == 64) {  // one field of 33..36 bits: up to three words
+        ow[wi] |= (uint32_t)(r << sh);
+        if (sh + BS > 32) ow[wi + 1] |= (uint32_t)(r >> (32 - sh));
+        if (sh + BS > 64) ow[wi + 2] |= (uint32_t)(r >> (64 - sh));
+      } else {
+        const uint32_t t = compact_l<BS, L>(r);
+        ow[wi] |= t << sh;
+        if (sh + K * BS > 32) ow[wi + 1] |= t >> (32 - sh);
+      }
     }
     sts_words<BS>(obuf, lane * BS, ow);
     __syncwarp();
@@ -581,10 +634,15 @@ __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t*
     __syncwarp();
   }
   cp_async_wait0_ge();
-  uint32_t o = orb;
-  if constexpr (L == 8) o = (o | (o >> 8) | (o >> 16) | (o >> 24)) & 0xffu;
-  if constexpr (L == 16) o = (o | (o >> 16)) & 0xffffu;
-  o = __reduce_or_sync(0xffffffffu, o);
+  uint64_t o;
+  if constexpr (L == 64) {
+    o = warp_or64(orb);
+  } else {
+    uint32_t o32 = orb;
+    if constexpr (L == 8) o32 = (o32 | (o32 >> 8) | (o32 >> 16) | (o32 >> 24)) & 0xffu;
+    if constexpr (L == 16) o32 = (o32 | (o32 >> 16)) & 0xffffu;
+    o = __reduce_or_sync(0xffffffffu, o32);
+  }
   const uint32_t ng = __reduce_or_sync(0xffffffffu, neg);
   if (lane == 0) {
     if (o) atomicOr(reinterpret_cast<unsigned long long*>(&out->stat_or), (unsigned long long)o);
@@ -592,9 +650,9 @@ __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t*
   }
 }
 
-// Calls lanes_body for the run-time (b, bs, mode).  Add: B <= 31 with
-// BS = B + 1; scale: B <= 31 with BS = B + D, 1 <= D <= kLaneGrow.  The lane
-// size is the smallest of 8, 16, 32 bits that holds BS.
+// Calls lanes_body for the run-time (b, bs, mode).  Add: B <= 32 with
+// BS = B + 1; scale: B <= 32 with BS = B + D, 1 <= D <= kLaneGrow.  The lane
+// size is lane_bits(BS).
 template <class Op, int B, int BS>
 __device__ __forceinline__ void lanes_modes(const Op& op, int mode, ccm_header* out,
                                             uint32_t* words, uint64_t n, uint32_t* sbuf) {
@@ -608,7 +666,7 @@ __device__ __forceinline__ void lanes_modes(const Op& op, int mode, ccm_header* 
 template <class Op, int B, int D = 1>
 __device__ __forceinline__ void lanes_grow(const Op& op, int d, int mode, ccm_header* out,
                                            uint32_t* words, uint64_t n, uint32_t* sbuf) {
-  if constexpr (B + D <= 32 && D <= Op::kLaneGrow) {
+  if constexpr (D <= Op::kLaneGrow) {
     if (d == D)
       lanes_modes<Op, B, B + D>(op, mode, out, words, n, sbuf);
     else
@@ -620,7 +678,7 @@ template <class Op, int B = 1>
 __device__ __forceinline__ void lanes_dispatch(const Op& op, int b, int bs, int mode,
                                                ccm_header* out, uint32_t* words, uint64_t n,
                                                uint32_t* sbuf) {
-  if constexpr (B <= 31) {
+  if constexpr (B <= 32) {
     if (b == B)
       lanes_grow<Op, B>(op, bs - B, mode, out, words, n, sbuf);
     else
@@ -638,11 +696,14 @@ __global__ void __launch_bounds__(kThreads) k_ew_lanes(Op op, ccm_header* out, u
   if (out->status != CCM_OK) return;
   op.init(n);
   const int bs = op.spec_width();
-  int B = (bs <= 32 && words_for(n, bs) <= capacity) ? op.lanes_width(bs) : 0;
+  int B = (bs <= 32 + Op::kLaneGrow && words_for(n, bs) <= capacity) ? op.lanes_width(bs) : 0;
   if (B && lane_body_words(B, bs, Op::kTwoInputs ? 2 : 1) > warp_words)
     B = 0;  // (buffers sized for narrower inputs)
   if (!B) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) out->reserved1 = 1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    out->reserved1 = 1;  // the lane pass wrote the result ...
+    out->reserved0 = bs;  // ... at this (speculative) width
+  }
   lanes_dispatch<Op>(op, B, bs, op.lanes_mode(), out, words, n,
                      s_lanes + (threadIdx.x / kWarp) * warp_words);
 }
@@ -1009,7 +1070,7 @@ int launch_ew_add(const EwCall& c, cudaStream_t st) {
   if (c.kind == EwKind::AddStats)
     k_ew<OpAdd, C, kStats><<<g, kThreads, 0, st>>>(op, c.out, nullptr, 0, n, 0);
   else if (c.kind == EwKind::AddSpec) {
-    launch_lanes_add(op, c.out, c.words, c.capacity, n, C < 31 ? C : 31, st);
+    launch_lanes_add(op, c.out, c.words, c.capacity, n, C, st);
     launched = 2;
     k_ew<OpAdd, C, kSpec><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity, n, 0);
   } else
@@ -1029,7 +1090,7 @@ int launch_ew_scale(const EwCall& c, cudaStream_t st) {
   } else if (c.kind == EwKind::ScaleSpec) {
     if constexpr (SMALL) {
       if (c.s != 0 && c.s > -32 && c.s < 32) {  // (the lane pass needs 1 <= |s| < 2^5)
-        launch_lanes_scale(op, c.out, c.words, c.capacity, n, C < 31 ? C : 31, st);
+        launch_lanes_scale(op, c.out, c.words, c.capacity, n, C, st);
         launched = 2;
       }
     }

@@ -354,10 +354,20 @@ void run_add(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, void
     profile_end(st);
     return;
   }
+  // No width class holds the output bound.  With inputs of at most 32 bits
+  // the lane pass may still write the sum (up to 33 bits) first; the
+  // run-time passes then return at once.
   ProdAdd p{{a.hdr, a.words, 0, 0}, {b.hdr, b.words, 0, 0}};
-  if (n) launch_stats(p, c.hdr, n, st);
+  const int in_bound = max(width_bound(a.capacity, n), width_bound(b.capacity, n));
+  const int lanes = n && in_bound <= 32;
   profile_begin(st);
-  launch_pack(p, c.hdr, c.words, c.capacity, n, st);
+  if (lanes) {
+    const ge::OpAdd op{ge::PackedIn{a.hdr, a.words, 0, 0, 0}, ge::PackedIn{b.hdr, b.words, 0, 0, 0}};
+    ge::launch_lanes_add(op, c.hdr, c.words, c.capacity, n, in_bound, st);
+    note_launch();
+  }
+  if (n) launch_stats(p, c.hdr, n, st, lanes);
+  launch_pack(p, c.hdr, c.words, c.capacity, n, st, lanes);
   profile_end(st);
 }
 
@@ -393,10 +403,20 @@ void run_scale(const ccm_matrix& a, int64_t s, const ccm_matrix& c, void* /*ws*/
     profile_end(st);
     return;
   }
+  // No width class holds the output bound: the lane pass may still write
+  // s A (up to 36 bits) first for 1 <= |s| < 2^5; the run-time passes then
+  // return at once.
   ProdScale p{{a.hdr, a.words, 0, 0}, s};
-  if (n) launch_stats(p, c.hdr, n, st);
+  const int in_bound = width_bound(a.capacity, n);
+  const int lanes = n && in_bound <= 32 && s != 0 && s > -32 && s < 32;
   profile_begin(st);
-  launch_pack(p, c.hdr, c.words, c.capacity, n, st);
+  if (lanes) {
+    const ge::OpScale<true> op{ge::PackedIn{a.hdr, a.words, 0, 0, 0}, s};
+    ge::launch_lanes_scale(op, c.hdr, c.words, c.capacity, n, in_bound, st);
+    note_launch();
+  }
+  if (n) launch_stats(p, c.hdr, n, st, lanes);
+  launch_pack(p, c.hdr, c.words, c.capacity, n, st, lanes);
   profile_end(st);
 }
 

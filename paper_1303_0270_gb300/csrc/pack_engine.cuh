@@ -97,9 +97,13 @@ __global__ void k_init(InitArgs a);
 // ---------------------------------------------------------------------------
 // k_stats
 // ---------------------------------------------------------------------------
+// `after_lanes`: an add/scale whose lane pass may have run first (it marks
+// the header, reserved1 = 1, and leaves the exact statistics there).
 template <class P>
-__global__ void __launch_bounds__(kStatsThreads) k_stats(P prod, ccm_header* out, uint64_t n) {
+__global__ void __launch_bounds__(kStatsThreads) k_stats(P prod, ccm_header* out, uint64_t n,
+                                                         int after_lanes) {
   if (out->status != CCM_OK) return;
+  if (after_lanes && out->reserved1) return;
   prod.init();
   uint64_t orv = 0;
   uint32_t neg = 0;
@@ -165,11 +169,14 @@ __device__ __forceinline__ bool resolve_output(ccm_header* out, uint32_t* words,
 
 template <class P>
 __global__ void __launch_bounds__(kPackThreads) k_pack(P prod, ccm_header* out, uint32_t* words,
-                                                       uint64_t capacity, uint64_t n) {
+                                                       uint64_t capacity, uint64_t n,
+                                                       int after_lanes) {
   __shared__ uint32_t s_lo[kPackWarps][kTilePad];
   __shared__ uint32_t s_hi[kPackWarps][kTilePad];
   int b, sgn;
   if (!resolve_output(out, words, capacity, n, b, sgn)) return;
+  // the lane pass wrote every field at the exact width: nothing left to do
+  if (after_lanes && out->reserved1 && b == (int)out->reserved0) return;
   prod.init();
   const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
   uint32_t* lo_t = s_lo[warp];
@@ -221,20 +228,21 @@ __global__ void __launch_bounds__(kPackThreads) k_pack(P prod, ccm_header* out, 
 int num_sms();
 void note_launch(int count);
 template <class P>
-void launch_stats(const P& prod, ccm_header* out, uint64_t n, cudaStream_t st) {
+void launch_stats(const P& prod, ccm_header* out, uint64_t n, cudaStream_t st,
+                  int after_lanes = 0) {
   uint64_t want = (n + kStatsThreads * 8 - 1) / (kStatsThreads * 8);
   int grid = (int)umin(umax(want, 1), (uint64_t)num_sms() * 8);
-  k_stats<P><<<grid, kStatsThreads, 0, st>>>(prod, out, n);
+  k_stats<P><<<grid, kStatsThreads, 0, st>>>(prod, out, n, after_lanes);
   note_launch();
 }
 
 template <class P>
 void launch_pack(const P& prod, ccm_header* out, uint32_t* words, uint64_t capacity, uint64_t n,
-                 cudaStream_t st) {
+                 cudaStream_t st, int after_lanes = 0) {
   uint64_t tiles = (n + kTileFields - 1) / kTileFields;
   uint64_t want = (tiles + kPackWarps - 1) / kPackWarps;
   int grid = (int)umin(umax(want, 1), (uint64_t)num_sms() * 16);
-  k_pack<P><<<grid, kPackThreads, 0, st>>>(prod, out, words, capacity, n);
+  k_pack<P><<<grid, kPackThreads, 0, st>>>(prod, out, words, capacity, n, after_lanes);
   note_launch();
 }
 

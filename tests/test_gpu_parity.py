@@ -309,6 +309,38 @@ def test_add_speculative_width(ccm, ba, sa, bb, sb, hit):
     assert_same_packed(got, expect, f"add spec {ba}/{sa} + {bb}/{sb} hit={hit}")
 
 
+@pytest.mark.parametrize("b,sgn", [(29, 1), (30, 0), (31, 1), (31, 0), (32, 1), (32, 0)])
+@pytest.mark.parametrize("cap", [None, 64])
+@pytest.mark.parametrize("hit", [True, False])
+def test_add_lanes_wide(ccm, b, sgn, cap, hit):
+    """Same-width add of 29..32-bit operands with an output capacity of
+    b + 1 bits (a width class when that is at most 32) or of 64 bits (no
+    width class): the lane pass writes the sum (64-bit lanes for a 33-bit
+    sum) and the remaining passes return at once or re-pack; word-identical
+    to the oracle, and the lane pass ran."""
+    shape = (3, 2011)
+    lo, hi = synth.signed_range(b) if sgn else (0, (1 << b) - 1)
+    a = _rand(b * 13 + sgn, shape, b, bool(sgn))
+    c = _rand(b * 17 + sgn, shape, b, bool(sgn))
+    if hit:
+        a.flat[0], c.flat[0] = hi, hi
+        a.flat[1], c.flat[1] = lo, lo
+    else:  # both operands keep width b and sign; every sum fits b bits
+        a, c = np.clip(a, lo // 2, hi // 2), np.clip(c, lo // 2, hi // 2)
+        ext = lo if sgn else hi
+        a.flat[0], c.flat[0] = ext, 0
+        a.flat[1], c.flat[1] = 0, ext
+    oa, oc = oracle.pack(a), oracle.pack(c)
+    expect = oracle.add(oa, oc)
+    pa = ccm.pack(to_dev(a), capacity=ccm.words_for(*shape, b))
+    pc = ccm.pack(to_dev(c), capacity=ccm.words_for(*shape, b))
+    out = ccm.PackedMatrix(*shape, ccm.words_for(*shape, cap or b + 1), device())
+    ccm.add_into(pa, pc, out)
+    assert_same_packed(out, expect, f"add lanes wide b={b} sgn={sgn} cap={cap} hit={hit}")
+    same = (oa.width, oa.is_signed) == (oc.width, oc.is_signed)
+    assert out.header().reserved1 == int(same), f"lane pass use b={b} sgn={sgn}"
+
+
 @pytest.mark.parametrize("b,sgn", [(5, 0), (1, 0), (3, 0), (8, 0), (4, 1), (12, 1), (20, 0)])
 @pytest.mark.parametrize("s", [7, -7, 8, 1, 0, 2, -1, 3000, -40000])
 def test_scale_speculative_width(ccm, b, sgn, s):
@@ -337,17 +369,19 @@ def _range_width(lo, hi):
 
 
 def _scale_lanes_expected(b, sgn, s, bs):
-    """Whether the scale lane pass applies: 1 <= |s| < 32, A of at most 31
-    bits, 1 <= bs - b <= 4, b + bitlen|s| at most the lane size of bs, and
-    not 1-bit signed A with s < 0."""
+    """Whether the scale lane pass applies: 1 <= |s| < 32, A of at most 32
+    bits, 1 <= bs - b <= 4, b + bitlen|s| at most the lane size of bs (8, 16,
+    32, or 64 bits for 33..36-bit results), and not 1-bit signed A with
+    s < 0."""
     t = abs(s)
-    lane = 8 if bs <= 8 else (16 if bs <= 16 else 32)
-    return 1 <= t < 32 and b <= 31 and 1 <= bs - b <= 4 and bs <= 32 and \
+    lane = 8 if bs <= 8 else (16 if bs <= 16 else (32 if bs <= 32 else 64))
+    return 1 <= t < 32 and b <= 32 and 1 <= bs - b <= 4 and \
         b + t.bit_length() <= lane and not (sgn and b == 1 and s < 0)
 
 
 @pytest.mark.parametrize("b,sgn", [(1, 0), (1, 1), (3, 0), (5, 0), (7, 1), (8, 1), (12, 1),
-                                   (13, 0), (16, 1), (20, 1), (27, 1), (28, 0), (29, 1), (31, 1)])
+                                   (13, 0), (16, 1), (20, 1), (27, 1), (28, 0), (29, 1), (31, 1),
+                                   (31, 0), (32, 1), (32, 0)])
 @pytest.mark.parametrize("s", [2, -1, -2, 3, 7, -7, 8, -8, 15, -16, 31, -31])
 def test_scale_lanes(ccm, b, sgn, s):
     """Scale through the lane pass (offset binary for signed A or negative s),
@@ -375,8 +409,8 @@ def test_scale_lanes(ccm, b, sgn, s):
         alo, ahi = synth.signed_range(oa.width) if oa.is_signed else (0, (1 << oa.width) - 1)
         spec = _range_width(*sorted((s * alo, s * ahi)))
         n = shape[0] * shape[1]
-        cls_ok = max(min(m.capacity * 32 // n, 64) for m in (pa, out)) <= 32  # width class
-        lanes = cls_ok and \
+        a_ok = min(pa.capacity * 32 // n, 64) <= 32  # the input's capacity bound
+        lanes = a_ok and \
             _scale_lanes_expected(oa.width, oa.is_signed, s, spec)
         assert out.header().reserved1 == int(lanes), \
             f"lane pass use b={oa.width} sgn={oa.is_signed} s={s} spec={spec}"
