@@ -346,8 +346,8 @@ def test_add_lanes_wide(ccm, b, sgn, cap, hit):
 def test_scale_speculative_width(ccm, b, sgn, s):
     """One-pass scale: s times the range of A's width; the maximum entry at the
     range top (hit) and below it (the exact width may be smaller: second pass).
-    Non-negative A of at most 8 bits with s >= 0 and a product range within 8
-    bits takes the byte-lane pass."""
+    For 1 <= |s| < 32 the lane pass writes C (see test_scale_lanes for the
+    cases it takes); larger |s| and s = 0 take the general passes."""
     shape = (7, 2049)
     a = _rand(b * 3 + sgn, shape, b, bool(sgn))
     for top in (True, False):
