@@ -102,11 +102,6 @@ struct Args {
 
 __device__ __forceinline__ int stage_pos(int w, int b) { return (b & 1) ? w : w + (w >> 5); }
 
-__device__ __forceinline__ void cp_async4(uint32_t* smem, const uint32_t* gmem, uint32_t bytes) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(bytes)
-               : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -131,16 +126,23 @@ __device__ __forceinline__ Chunk chunk_of(const Mat& M, const Unit& u, uint32_t 
   return {w_first, (uint32_t)(((end_bit + 31) >> 5) - w_first) + 1};
 }
 
-// cp.async of a chunk's words into a slot (words past the matrix's data
-// words are zero-filled).
+// cp.async of a chunk's words into a slot: the words inside the matrix's
+// data are copied, the rest of the chunk (past the data, at the matrix's
+// end) is zero-filled.  Word w goes to stage_pos(w), so from one lane's
+// word to its next (32 on) the destination steps by 32 or 33 words.
 template <int B>
 __device__ __forceinline__ void issue_chunk(const uint32_t* __restrict__ wa, uint64_t dw, Chunk c,
                                             uint32_t* slot, int lane) {
-  for (uint32_t w = lane; w < c.nwords; w += 32) {
-    const uint64_t g = c.w_first + w;
-    const bool in = g < dw;
-    cp_async4(slot + stage_pos((int)w, B), wa + (in ? g : 0), in ? 4u : 0u);
-  }
+  const uint32_t nin =
+      (uint32_t)min((uint64_t)c.nwords, dw > c.w_first ? dw - c.w_first : (uint64_t)0);
+  constexpr unsigned kStep = 4 * ((B & 1) ? 32 : 33);
+  unsigned dst = (unsigned)__cvta_generic_to_shared(slot) + 4 * lane;  // stage_pos(lane) = lane
+  const uint32_t* src = wa + c.w_first + lane;
+  uint32_t w = lane;
+  for (; w < nin; w += 32, src += 32, dst += kStep)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+  for (; w < c.nwords; w += 32, dst += kStep)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, 0;\n" ::"r"(dst), "l"(wa) : "memory");
 }
 
 // ---------------------------------------------------------------------------
