@@ -362,9 +362,12 @@ ccm_status ccm_matvec_static(const ccm_matrix* a, const ccm_matrix* x, const ccm
  * cudaEventRecord(stop) after it, on that call's stream, so the caller can
  * time that one kernel with cudaEventElapsedTime.  `start` and `stop` are
  * cudaEvent_t handles owned by the caller; NULL, NULL cancels.  The main
- * kernel is: k_pack for ccm_pack, the two passes of ccm_add/ccm_scale
- * (together), k_stats for ccm_measure,
- * k_unpack, k_get, and the product kernel of ccm_matvec/ccm_matmul. */
+ * kernel is: for ccm_pack the local pack (with a workspace; the re-code to
+ * the matrix width that follows is not bracketed) or the pack pass (without
+ * one), every pass of ccm_add/ccm_scale after the initialisation
+ * (together: the lane pass and the general passes), k_stats for
+ * ccm_measure, k_unpack, k_get, and the product kernel of
+ * ccm_matvec/ccm_matmul. */
 uint64_t ccm_launch_count(void);
 ccm_status ccm_profile_next(void* start_event, void* stop_event);
 
