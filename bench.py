@@ -11,7 +11,10 @@ Default workload (one "step" = one pass of the whole hot path):
   L2, so every step streams them from HBM.
 
 Printed: one JSON line (rank 0).  `value` is the step's algorithmic bytes
-(the one-pass traffic of each operation) divided by the
+(the one-pass traffic of each operation: dense int64 read and packed bytes
+written for pack, the reverse for unpack, packed inputs plus packed result
+for add and scale, packed A plus x and y for matvec, index, value and one
+word per gathered entry for get) divided by the
 device-timed step time, summed over ranks.
 """
 from __future__ import annotations
