@@ -273,7 +273,7 @@ typedef struct ccm_batch_info {
   uint32_t units;         /* work units */
   uint64_t y_rows;        /* sum of the entries' rows */
   uint32_t unit_segments; /* segments per unit */
-  uint32_t max_cols;      /* widest entry (sizes the kernel's shared memory) */
+  uint32_t max_cols;      /* widest entry (at most 8192 columns) */
   uint64_t plan_bytes;
   uint32_t max_width;     /* widest A the capacities admit, <= 32 (sizes the staging) */
   uint32_t reserved;
