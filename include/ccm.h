@@ -37,7 +37,8 @@
  *    unless documented as synchronous.
  *  - Host-detectable errors (NULL pointers, bad dtype, shape mismatch,
  *    too-small capacity or workspace) return a negative ccm_status at once and
- *    launch nothing.
+ *    launch nothing.  A shape whose rows*cols exceeds 2^57 fields (or wraps
+ *    uint64) is CCM_E_INVAL; ccm_workspace_bytes returns SIZE_MAX for it. 
  *  - Data-dependent errors (int64 overflow of a result, a result whose width
  *    needs more words than the output capacity, an input header that is not a
  *    valid matrix) are written by the GPU into the output header's `status`;
@@ -128,6 +129,26 @@ typedef enum ccm_matmul_path {
  * restated for 32-bit words and 16-byte padding).  0 for an empty matrix or a
  * width outside 1..64. */
 uint64_t ccm_words_for(uint64_t rows, uint64_t cols, int width);
+
+/* Result-width bounds (Methods, Method 1: Eq. 1, with this library's signed
+ * reading, applied to the range of every result that operands of the given
+ * widths and sign modes allow; a b-bit field holds [0, 2^b - 1] unsigned or
+ * [-2^(b-1), 2^(b-1) - 1] signed).  Each returns the smallest width that holds
+ * any possible result, so an output of ccm_words_for(rows, cols, bound) words
+ * can never be short of capacity; the exact width of an actual result may be
+ * smaller.  The bound is capped at 64: a result beyond int64 is reported by
+ * the operation itself as CCM_E_OVERFLOW.  A width outside 1..64 returns
+ * CCM_E_WIDTH (negative).  Pure host functions: no GPU, no synchronisation
+ * (read the operand widths with ccm_header_read first).
+ *  ccm_bound_add:    C = A + B; range [lo_A + lo_B, hi_A + hi_B].
+ *  ccm_bound_scale:  C = s A; range s * [lo_A, hi_A].
+ *  ccm_bound_matvec: y = A x with `cols` columns: cols times the smallest and
+ *                    the largest product of the range ends (1 when cols = 0).
+ *  ccm_bound_matmul: C = A B with inner size `inner`, the same rule. */
+int ccm_bound_add(int width_a, int signed_a, int width_b, int signed_b);
+int ccm_bound_scale(int width_a, int signed_a, int64_t s);
+int ccm_bound_matvec(int width_a, int signed_a, int width_x, int signed_x, uint64_t cols);
+int ccm_bound_matmul(int width_a, int signed_a, int width_b, int signed_b, uint64_t inner);
 
 /* Human-readable name of a status code (static storage). */
 const char* ccm_status_str(int status);
@@ -339,9 +360,12 @@ ccm_status ccm_vlb_matvec(const ccm_header* hdr, const uint32_t* words, uint64_t
  * ccm_matvec, minus the workspace: the scratch is a fixed array of
  * CCM_STATIC_SCRATCH_BYTES compiled into libccm, present on every GPU that
  * loads the library until the process exits.
- *  - Size limit: the matvec scratch for A (rows x cols) is 8*cols + 8*rows
- *    bytes plus alignment; larger problems return CCM_E_CAPACITY at once
- *    (rows + cols up to about 131,000).
+ *  - Size limit: A (rows x cols) needs up256(8*cols) + up256(8*rows) + 256
+ *    bytes of it (up256 rounds up to a multiple of 256), as
+ *    ccm_workspace_bytes(CCM_OP_MATVEC, rows, cols, 1) reports; larger
+ *    problems return CCM_E_CAPACITY at once, before any other check but the
+ *    NULL and shape checks (rows + cols up to about 131,000: rows = 4 allows
+ *    up to 131,520 columns).  The other host checks are ccm_matvec's.
  *  - The first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress, with that device current); make that first call
  *    before any stream capture.

@@ -26,7 +26,7 @@ class BatchMatvec:
         if ys is None:
             ys = []
             for a, x in zip(self.mats, self.xs):
-                bound = min(64, a.width_bound() + x.width_bound() + int(a.cols).bit_length() + 1)
+                bound = ccm.bound_matvec(a, x)
                 ys.append(ccm.PackedMatrix(a.rows, 1, ccm.words_for(a.rows, 1, bound), self.device))
         self.ys = list(ys)
         n = len(self.mats)

@@ -93,6 +93,10 @@ SIGNATURES = {
     "ccm_vlb_unpack": ([_vp, _vp, _u64, _vp, _u64, _u64, _vp, _i32, _vp, _vp], _i32),
     "ccm_matvec2": ([_MP, _MP, _MP, _MP, _MP, _vp, _sz, _vp], _i32),
     "ccm_vlb_matvec": ([_vp, _vp, _u64, _vp, _u64, _u64, _MP, _MP, _vp, _sz, _vp], _i32),
+    "ccm_bound_add": ([_i32, _i32, _i32, _i32], _i32),
+    "ccm_bound_scale": ([_i32, _i32, _i64], _i32),
+    "ccm_bound_matvec": ([_i32, _i32, _i32, _i32, _u64], _i32),
+    "ccm_bound_matmul": ([_i32, _i32, _i32, _i32, _u64], _i32),
     "ccm_launch_count": ([], _u64),
     "ccm_profile_next": ([_vp, _vp], _i32),
 }
@@ -146,10 +150,6 @@ def _stream(stream=None) -> ctypes.c_void_p:
 
 def words_for(rows: int, cols: int, width: int) -> int:
     return int(lib().ccm_words_for(rows, cols, width))
-
-
-def _bitlen(v: int) -> int:
-    return int(abs(int(v))).bit_length()
 
 
 class PackedMatrix:
@@ -217,8 +217,6 @@ class PackedMatrix:
     def header_tensor(self) -> torch.Tensor:
         return self.buf[:HEADER_WORDS]
 
-    def width_bound(self) -> int:
-        return self.width
 
 
 def _as_dense(t: torch.Tensor):
@@ -305,8 +303,30 @@ def get(a: PackedMatrix, idx: torch.Tensor, stream=None, check: bool = True) -> 
     return out
 
 
-def _bound_capacity(rows, cols, bound):
-    return words_for(rows, cols, max(1, min(64, bound)))
+def _bound(status: int, what: str) -> int:
+    if status < 0:
+        raise CCMError(status, what)
+    return int(status)
+
+
+def bound_add(a: PackedMatrix, b: PackedMatrix) -> int:
+    """Width that holds every possible A + B (ccm_bound_add)."""
+    return _bound(lib().ccm_bound_add(a.width, a.is_signed, b.width, b.is_signed),
+                  "ccm_bound_add")
+
+
+def bound_scale(a: PackedMatrix, s: int) -> int:
+    return _bound(lib().ccm_bound_scale(a.width, a.is_signed, int(s)), "ccm_bound_scale")
+
+
+def bound_matvec(a: PackedMatrix, x: PackedMatrix) -> int:
+    return _bound(lib().ccm_bound_matvec(a.width, a.is_signed, x.width, x.is_signed, a.cols),
+                  "ccm_bound_matvec")
+
+
+def bound_matmul(a: PackedMatrix, b: PackedMatrix) -> int:
+    return _bound(lib().ccm_bound_matmul(a.width, a.is_signed, b.width, b.is_signed, a.cols),
+                  "ccm_bound_matmul")
 
 
 def add_into(a: PackedMatrix, b: PackedMatrix, c: PackedMatrix, stream=None) -> PackedMatrix:
@@ -319,7 +339,7 @@ def add_into(a: PackedMatrix, b: PackedMatrix, c: PackedMatrix, stream=None) -> 
 
 def add(a: PackedMatrix, b: PackedMatrix, capacity: int | None = None, stream=None):
     if capacity is None:
-        capacity = _bound_capacity(a.rows, a.cols, max(a.width_bound(), b.width_bound()) + 2)
+        capacity = words_for(a.rows, a.cols, bound_add(a, b))
     return add_into(a, b, PackedMatrix(a.rows, a.cols, capacity, a.device), stream)
 
 
@@ -333,7 +353,7 @@ def scale_into(a: PackedMatrix, s: int, c: PackedMatrix, stream=None) -> PackedM
 
 def scale(a: PackedMatrix, s: int, capacity: int | None = None, stream=None):
     if capacity is None:
-        capacity = _bound_capacity(a.rows, a.cols, a.width_bound() + _bitlen(s) + 1)
+        capacity = words_for(a.rows, a.cols, bound_scale(a, s))
     return scale_into(a, s, PackedMatrix(a.rows, a.cols, capacity, a.device), stream)
 
 
@@ -359,8 +379,7 @@ def matvec_into(a: PackedMatrix, x: PackedMatrix, y: PackedMatrix, ws: torch.Ten
 
 def matvec(a: PackedMatrix, x: PackedMatrix, capacity: int | None = None, stream=None):
     if capacity is None:
-        capacity = _bound_capacity(a.rows, 1, a.width_bound() + x.width_bound() +
-                                   _bitlen(a.cols) + 1)
+        capacity = words_for(a.rows, 1, bound_matvec(a, x))
     return matvec_into(a, x, PackedMatrix(a.rows, 1, capacity, a.device), stream=stream)
 
 
@@ -406,8 +425,7 @@ def matmul_into(a: PackedMatrix, b: PackedMatrix, c: PackedMatrix, path: int = M
 def matmul(a: PackedMatrix, b: PackedMatrix, path: int = MATMUL_AUTO,
            capacity: int | None = None, stream=None):
     if capacity is None:
-        capacity = _bound_capacity(a.rows, b.cols, a.width_bound() + b.width_bound() +
-                                   _bitlen(a.cols) + 1)
+        capacity = words_for(a.rows, b.cols, bound_matmul(a, b))
     return matmul_into(a, b, PackedMatrix(a.rows, b.cols, capacity, a.device), path, stream=stream)
 
 

@@ -15,7 +15,7 @@ using ccm::words_for;
 cudaStream_t to_cuda(ccm_stream_t s) { return reinterpret_cast<cudaStream_t>(s); }
 
 bool valid_out(const ccm_matrix* m) {
-  if (!m || !m->hdr) return false;
+  if (!m || !m->hdr || !ccm::shape_ok(m->rows, m->cols)) return false;
   if (m->capacity && !m->words) return false;
   if (reinterpret_cast<uintptr_t>(m->hdr) % 16 || reinterpret_cast<uintptr_t>(m->words) % 16)
     return false;
@@ -23,7 +23,7 @@ bool valid_out(const ccm_matrix* m) {
 }
 
 bool valid_in(const ccm_matrix* m) {
-  if (!m || !m->hdr) return false;
+  if (!m || !m->hdr || !ccm::shape_ok(m->rows, m->cols)) return false;
   if (m->rows * m->cols && !m->words) return false;
   return reinterpret_cast<uintptr_t>(m->hdr) % 16 == 0 &&
          reinterpret_cast<uintptr_t>(m->words) % 16 == 0;
@@ -38,6 +38,16 @@ ccm_status launched() {
 bool capacity_ok(const ccm_matrix* m) { return m->capacity >= words_for(m->rows * m->cols, 1); }
 
 }  // namespace
+
+namespace ccm {
+ccm_status matvec_host_check(const ccm_matrix* a, const ccm_matrix* x, const ccm_matrix* y) {
+  if (!valid_in(a) || !valid_in(x) || !valid_out(y)) return CCM_E_INVAL;
+  if (x->rows != a->cols || x->cols != 1 || y->rows != a->rows || y->cols != 1)
+    return CCM_E_SHAPE;
+  if (!capacity_ok(y)) return CCM_E_CAPACITY;
+  return CCM_OK;
+}
+}  // namespace ccm
 
 extern "C" {
 
@@ -65,7 +75,7 @@ int ccm_version(void) { return 100; }
 
 ccm_status ccm_measure(const void* dense, int dtype, uint64_t rows, uint64_t cols,
                        ccm_header* hdr, ccm_stream_t stream) {
-  if (!hdr || (rows * cols && !dense)) return CCM_E_INVAL;
+  if (!hdr || !ccm::shape_ok(rows, cols) || (rows * cols && !dense)) return CCM_E_INVAL;
   if (dtype != CCM_I32 && dtype != CCM_I64) return CCM_E_INVAL;
   ccm::run_measure(dense, dtype, rows, cols, hdr, to_cuda(stream));
   return launched();
@@ -73,7 +83,7 @@ ccm_status ccm_measure(const void* dense, int dtype, uint64_t rows, uint64_t col
 
 ccm_status ccm_pack(const void* dense, int dtype, uint64_t rows, uint64_t cols,
                     const ccm_matrix* out, void* ws, size_t ws_bytes, ccm_stream_t stream) {
-  if (!valid_out(out) || (rows * cols && !dense)) return CCM_E_INVAL;
+  if (!valid_out(out) || !ccm::shape_ok(rows, cols) || (rows * cols && !dense)) return CCM_E_INVAL;
   if (dtype != CCM_I32 && dtype != CCM_I64) return CCM_E_INVAL;
   if (out->rows != rows || out->cols != cols) return CCM_E_SHAPE;
   if (!capacity_ok(out)) return CCM_E_CAPACITY;
@@ -120,6 +130,12 @@ ccm_status ccm_scale(const ccm_matrix* a, int64_t s, const ccm_matrix* c, void* 
 }
 
 size_t ccm_workspace_bytes(int op, uint64_t m, uint64_t k, uint64_t n) {
+  // shapes whose sizes would wrap: saturated, never a small wrapped value
+  using ccm::shape_ok;
+  if (op == CCM_OP_MATMUL && !(shape_ok(m, k) && shape_ok(k, n) && shape_ok(m, n)))
+    return SIZE_MAX;
+  if ((op == CCM_OP_PACK || op == CCM_OP_VLB) && !shape_ok(m, k)) return SIZE_MAX;
+  if (op == CCM_OP_VLB_MATVEC && m > ccm::kMaxFields) return SIZE_MAX;
   switch (op) {
     case CCM_OP_MATVEC: return ccm::matvec_workspace(m, k);
     case CCM_OP_PACK: return ccm::pack_workspace(m, k, n);
@@ -132,11 +148,9 @@ size_t ccm_workspace_bytes(int op, uint64_t m, uint64_t k, uint64_t n) {
 
 ccm_status ccm_matvec(const ccm_matrix* a, const ccm_matrix* x, const ccm_matrix* y, void* ws,
                       size_t ws_bytes, ccm_stream_t stream) {
-  if (!valid_in(a) || !valid_in(x) || !valid_out(y) || !ws) return CCM_E_INVAL;
-  if (reinterpret_cast<uintptr_t>(ws) % 256) return CCM_E_INVAL;
-  if (x->rows != a->cols || x->cols != 1 || y->rows != a->rows || y->cols != 1)
-    return CCM_E_SHAPE;
-  if (!capacity_ok(y)) return CCM_E_CAPACITY;
+  const ccm_status hc = ccm::matvec_host_check(a, x, y);
+  if (hc != CCM_OK) return hc;
+  if (!ws || reinterpret_cast<uintptr_t>(ws) % 256) return CCM_E_INVAL;
   if (ws_bytes < ccm::matvec_workspace(a->rows, a->cols)) return CCM_E_CAPACITY;
   ccm::run_matvec(*a, *x, *y, ws, to_cuda(stream));
   return launched();
@@ -178,7 +192,7 @@ uint64_t ccm_vlb_index_entries(uint64_t rows, uint64_t cols) {
 ccm_status ccm_vlb_pack(const void* dense, int dtype, uint64_t rows, uint64_t cols,
                         ccm_header* hdr, uint32_t* words, uint64_t capacity, uint64_t* index,
                         void* ws, size_t ws_bytes, ccm_stream_t stream) {
-  if (!hdr || !ws || (rows * cols && !dense)) return CCM_E_INVAL;
+  if (!hdr || !ws || !ccm::shape_ok(rows, cols) || (rows * cols && !dense)) return CCM_E_INVAL;
   if (dtype != CCM_I32 && dtype != CCM_I64) return CCM_E_INVAL;
   if (words && !index) return CCM_E_INVAL;
   if (reinterpret_cast<uintptr_t>(hdr) % 16 || reinterpret_cast<uintptr_t>(ws) % 256)
@@ -191,7 +205,8 @@ ccm_status ccm_vlb_pack(const void* dense, int dtype, uint64_t rows, uint64_t co
 ccm_status ccm_vlb_unpack(const ccm_header* hdr, const uint32_t* words, uint64_t capacity,
                           const uint64_t* index, uint64_t rows, uint64_t cols, void* dense,
                           int dtype, int32_t* err, ccm_stream_t stream) {
-  if (!hdr || (rows * cols && (!words || !index || !dense))) return CCM_E_INVAL;
+  if (!hdr || !ccm::shape_ok(rows, cols) || (rows * cols && (!words || !index || !dense)))
+    return CCM_E_INVAL;
   if (dtype != CCM_I32 && dtype != CCM_I64) return CCM_E_INVAL;
   if (rows * cols == 0) return CCM_OK;
   ccm::run_vlb_unpack(hdr, words, capacity, index, rows, cols, dense, dtype, err,
@@ -203,7 +218,8 @@ ccm_status ccm_vlb_matvec(const ccm_header* hdr, const uint32_t* words, uint64_t
                           const uint64_t* index, uint64_t rows, uint64_t cols,
                           const ccm_matrix* x, const ccm_matrix* y, void* ws, size_t ws_bytes,
                           ccm_stream_t stream) {
-  if (!hdr || !ws || !valid_in(x) || !valid_out(y)) return CCM_E_INVAL;
+  if (!hdr || !ws || !valid_in(x) || !valid_out(y) || !ccm::shape_ok(rows, cols))
+    return CCM_E_INVAL;
   if (rows * cols && (!words || !index)) return CCM_E_INVAL;
   if (reinterpret_cast<uintptr_t>(ws) % 256) return CCM_E_INVAL;
   if (x->rows != cols || x->cols != 1 || y->rows != rows || y->cols != 1) return CCM_E_SHAPE;

@@ -17,7 +17,15 @@ namespace ccm {
 constexpr int kWarp = 32;
 constexpr int kTileFields = 1024;  // one warp tile = 32 groups of 32 fields
 
+// Largest field count of one matrix: every bit offset n*64 then fits uint64.
+constexpr uint64_t kMaxFields = 1ull << 57;
+
 __host__ __device__ __forceinline__ uint64_t umin(uint64_t a, uint64_t b) { return a < b ? a : b; }
+
+// rows*cols neither wraps nor exceeds kMaxFields.
+__host__ __device__ __forceinline__ bool shape_ok(uint64_t rows, uint64_t cols) {
+  return rows == 0 || cols == 0 || rows <= kMaxFields / cols;
+}
 __host__ __device__ __forceinline__ uint64_t umax(uint64_t a, uint64_t b) { return a > b ? a : b; }
 
 struct Stats {

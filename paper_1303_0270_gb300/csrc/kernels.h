@@ -38,6 +38,9 @@ void run_scale(const ccm_matrix& a, int64_t s, const ccm_matrix& c, void* ws, si
 void run_pack_scratch(const int64_t* vals, const ccm_matrix& out, cudaStream_t st,
                       bool stats_done = false);
 
+// Host checks of ccm_matvec that need no workspace (pointers, alignment,
+// shapes, y's minimum capacity).
+ccm_status matvec_host_check(const ccm_matrix* a, const ccm_matrix* x, const ccm_matrix* y);
 size_t matvec_workspace(uint64_t m, uint64_t n);
 size_t matvec2_workspace(uint64_t m, uint64_t n1, uint64_t n2);
 void run_matvec2(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& b,

@@ -161,6 +161,8 @@ void launch(int bmax, const RowArgs& a, bool narrow, unsigned grid, int threads,
 }  // namespace mvf
 
 size_t matvec_workspace(uint64_t m, uint64_t n) {
+  // saturates instead of wrapping: a shape this large can never be served
+  if (m > kMaxFields || n > kMaxFields) return SIZE_MAX;
   auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
   return up(n * sizeof(int64_t)) + up(m * sizeof(int64_t)) + 256;
 }

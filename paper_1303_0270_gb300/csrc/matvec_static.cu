@@ -50,11 +50,18 @@ void* scratch_for_current_device() {
 
 extern "C" ccm_status ccm_matvec_static(const ccm_matrix* a, const ccm_matrix* x,
                                         const ccm_matrix* y, ccm_stream_t stream) {
-  if (!a || !x || !y || !a->hdr || !x->hdr || !y->hdr || !y->words) return CCM_E_INVAL;
+  // ccm_matvec's host checks apply unchanged (matvec_host_check below); the
+  // size limit comes first so that no size arithmetic can wrap
+  if (!a || !x || !y) return CCM_E_INVAL;
   if (x->rows != a->cols || x->cols != 1 || y->rows != a->rows || y->cols != 1)
     return CCM_E_SHAPE;
+  if (a->rows > CCM_STATIC_SCRATCH_BYTES / 8 || a->cols > CCM_STATIC_SCRATCH_BYTES / 8)
+    return CCM_E_CAPACITY;
   const size_t need = ccm::matvec_workspace(a->rows, a->cols);
   if (need > CCM_STATIC_SCRATCH_BYTES) return CCM_E_CAPACITY;  // too large for the fixed scratch
+  // every other host check before the first CUDA call
+  const ccm_status hc = ccm::matvec_host_check(a, x, y);
+  if (hc != CCM_OK) return hc;
   void* ws = ccm::scratch_for_current_device();
   if (!ws) return CCM_E_CUDA;
   return ccm_matvec(a, x, y, ws, CCM_STATIC_SCRATCH_BYTES, stream);

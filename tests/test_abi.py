@@ -109,3 +109,106 @@ def test_product_does_not_touch_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "ccm_oracle" not in text and "ccmo_" not in text, f
+
+
+def _range_width(lo, hi):
+    """The width rule on an integer range, written out: unsigned
+    max(1, bitlen(hi)) when lo >= 0, else the smallest two's complement
+    width holding both ends."""
+    if lo >= 0:
+        return max(1, hi.bit_length())
+    b = 1
+    while not (-(1 << (b - 1)) <= lo and hi <= (1 << (b - 1)) - 1):
+        b += 1
+    return b
+
+
+def _field_values(b, sgn):
+    return range(-(1 << (b - 1)), 1 << (b - 1)) if sgn else range(0, 1 << b)
+
+
+def test_bound_calls_match_brute_force(L):
+    """ccm_bound_*: the smallest width holding every result that operands of
+    the given widths allow, against enumeration of every operand value."""
+    for ba in range(1, 6):
+        for sa in (0, 1):
+            va = list(_field_values(ba, sa))
+            for bb in range(1, 6):
+                for sb in (0, 1):
+                    vb = list(_field_values(bb, sb))
+                    sums = [p + q for p in va for q in vb]
+                    assert L.ccm_bound_add(ba, sa, bb, sb) == _range_width(min(sums), max(sums))
+                    prods = [p * q for p in va for q in vb]
+                    for k in (0, 1, 2, 3, 1000):
+                        # sum of k products reaches k*min and k*max (all terms equal)
+                        want = 1 if k == 0 else _range_width(k * min(prods), k * max(prods))
+                        assert L.ccm_bound_matvec(ba, sa, bb, sb, k) == want
+                        assert L.ccm_bound_matmul(ba, sa, bb, sb, k) == want
+            for s in (-33, -7, -1, 0, 1, 2, 7, 31, 1 << 20):
+                sc = [s * p for p in va]
+                assert L.ccm_bound_scale(ba, sa, s) == _range_width(min(sc), max(sc))
+
+
+def test_bound_calls_small_exhaustive_sums(L):
+    """For k = 2 the bound is attained: enumerate every pair of products."""
+    for ba, sa, bb, sb in ((2, 1, 2, 0), (3, 0, 2, 1), (2, 1, 3, 1)):
+        va, vb = list(_field_values(ba, sa)), list(_field_values(bb, sb))
+        dots = [a0 * x0 + a1 * x1 for a0 in va for a1 in va for x0 in vb for x1 in vb]
+        assert L.ccm_bound_matvec(ba, sa, bb, sb, 2) == _range_width(min(dots), max(dots))
+
+
+def test_bound_calls_edges(L):
+    assert L.ccm_bound_add(64, 1, 64, 1) == 64       # beyond int64: capped, overflow is reported
+    assert L.ccm_bound_add(63, 1, 63, 1) == 64
+    assert L.ccm_bound_add(62, 0, 62, 0) == 63
+    assert L.ccm_bound_scale(64, 0, -(1 << 63)) == 64
+    assert L.ccm_bound_scale(10, 1, 0) == 1
+    assert L.ccm_bound_matvec(32, 1, 31, 1, 1 << 20) == 64
+    assert L.ccm_bound_matvec(5, 0, 8, 1, 8192) == 26
+    for bad in (0, 65, -3):
+        assert L.ccm_bound_add(bad, 0, 3, 0) == ccm.E_WIDTH
+        assert L.ccm_bound_scale(bad, 1, 3) == ccm.E_WIDTH
+        assert L.ccm_bound_matvec(3, 0, bad, 1, 5) == ccm.E_WIDTH
+        assert L.ccm_bound_matmul(bad, 0, 3, 0, 5) == ccm.E_WIDTH
+
+
+def test_workspace_sizes_saturate_instead_of_wrapping(L):
+    """Sizes whose byte counts would wrap uint64 come back as SIZE_MAX."""
+    size_max = (1 << (8 * ctypes.sizeof(ctypes.c_size_t))) - 1
+    assert L.ccm_workspace_bytes(ccm.OP_MATVEC, 1 << 61, 1, 0) == size_max
+    assert L.ccm_workspace_bytes(ccm.OP_MATVEC, 1, 1 << 61, 0) == size_max
+    assert L.ccm_workspace_bytes(ccm.OP_MATMUL, 1 << 40, 1 << 40, 1 << 40) == size_max
+    assert L.ccm_workspace_bytes(ccm.OP_PACK, 1 << 40, 1 << 40, 16) == size_max
+    assert L.ccm_workspace_bytes(ccm.OP_VLB, 1 << 40, 1 << 40, 0) == size_max
+    assert L.ccm_workspace_bytes(ccm.OP_MATVEC, 1000, 1000, 1) < 1 << 20
+    # shapes whose field count wraps are rejected before any launch
+    bp = ctypes.byref
+    huge = _m(1 << 33, 1 << 31)
+    assert L.ccm_scale(bp(huge), 2, bp(_m(1 << 33, 1 << 31)), None, 0, None) == ccm.E_INVAL
+
+
+STATIC_BYTES = (1 << 20) + 4096
+
+
+def _static_need(rows, cols):
+    up = lambda v: (v + 255) // 256 * 256  # noqa: E731
+    return up(8 * cols) + up(8 * rows) + 256
+
+
+def test_static_matvec_size_limit_boundary(L):
+    """ccm_matvec_static: the largest A that fits the fixed scratch passes the
+    size check (and then fails on a misaligned y, so nothing launches); one
+    column more returns CCM_E_CAPACITY; a size that would wrap the size
+    arithmetic is rejected too."""
+    bp = ctypes.byref
+    rows = 4
+    cols = max(c for c in range(131000, 132000) if _static_need(rows, c) <= STATIC_BYTES)
+    assert cols == 131520 and _static_need(rows, cols + 1) > STATIC_BYTES
+    assert L.ccm_workspace_bytes(ccm.OP_MATVEC, rows, cols, 1) == _static_need(rows, cols)
+    for c, want in ((cols, ccm.E_INVAL), (cols + 1, ccm.E_CAPACITY)):
+        a, x = _m(rows, c, cap=1 << 20), _m(c, 1, cap=1 << 16)
+        y_misaligned = _m(rows, 1, cap=16, words=0x2004)
+        assert L.ccm_matvec_static(bp(a), bp(x), bp(y_misaligned), None) == want
+    wrap = 1 << 61
+    a, x, y = _m(wrap, 1), _m(1, 1), _m(wrap, 1)
+    assert L.ccm_matvec_static(bp(a), bp(x), bp(y), None) == ccm.E_CAPACITY

@@ -2,10 +2,10 @@
 allocate device memory (their memory is reserved up front by another
 allocator, or they cannot afford the device-wide synchronisation of a
 cudaMalloc).  Its scratch is a fixed array inside libccm; this test calls it
-through the C ABI and checks that two calls in a row give exactly the words
+through the C ABI and checks that three calls in a row give exactly the words
 ccm_matvec gives with a caller-provided workspace (integer results: the
 tolerance is zero), including when the second call must not see what the
-first one left in the shared scratch."""
+earlier ones left in the shared scratch."""
 import ctypes
 
 import numpy as np
@@ -27,8 +27,11 @@ def test_static_scratch_matvec_matches_workspace_matvec():
     ccm = lib_ccm()
     L = ccm.lib()
     dev = device()
-    # two calls in a row: row-aligned (streaming kernel) then ragged (row kernel)
-    for seed, (m, n, b) in ((11, (1000, 1024, 7)), (12, (333, 777, 19))):
+    # calls in a row: row-aligned (streaming kernel), ragged (row kernel), then
+    # a smaller row-aligned one that finds the larger call's y sums and x
+    # still in the shared scratch beyond its own rows and columns
+    for seed, (m, n, b) in ((11, (1000, 1024, 7)), (12, (333, 777, 19)),
+                            (13, (96, 256, 12))):
         pa, px = _case(ccm, seed, m, n, b)
         ref = ccm.matvec(pa, px, capacity=ccm.words_for(m, 1, 64))
         out = ccm.PackedMatrix(m, 1, ccm.words_for(m, 1, 64), dev)
