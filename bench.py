@@ -125,15 +125,20 @@ class Workload:
         self.X = ccm.gen_uniform(N_COLS, sa, synth.STREAM_X, -128, 127, device=dev).view(N_COLS, 1)
         self.idx = ccm.gen_uniform(GET_COUNT, sa, synth.STREAM_INDEX, 0, n - 1, device=dev)
         self.seeds = (sa, sb)
-        ba, _ = ccm.measure(self.A)
-        bb, _ = ccm.measure(self.B)
-        bx, _ = ccm.measure(self.X)
+        ba, sa = ccm.measure(self.A)
+        bb, sb = ccm.measure(self.B)
+        bx, sx = ccm.measure(self.X)
+        L = ccm.lib()
+        # outputs sized by the library's result-width bounds
+        bc = L.ccm_bound_add(ba, sa, bb, sb)
+        bd = L.ccm_bound_scale(ba, sa, SCALE)
+        by = L.ccm_bound_matvec(ba, sa, bx, sx, N_COLS)
         self.pa = ccm.PackedMatrix(N_ROWS, N_COLS, ccm.words_for(N_ROWS, N_COLS, ba), dev)
         self.pb = ccm.PackedMatrix(N_ROWS, N_COLS, ccm.words_for(N_ROWS, N_COLS, bb), dev)
         self.px = ccm.PackedMatrix(N_COLS, 1, ccm.words_for(N_COLS, 1, bx), dev)
-        self.pc = ccm.PackedMatrix(N_ROWS, N_COLS, ccm.words_for(N_ROWS, N_COLS, max(ba, bb) + 2), dev)
-        self.pd = ccm.PackedMatrix(N_ROWS, N_COLS, ccm.words_for(N_ROWS, N_COLS, ba + 4), dev)
-        self.py = ccm.PackedMatrix(N_ROWS, 1, ccm.words_for(N_ROWS, 1, ba + bx + 15), dev)
+        self.pc = ccm.PackedMatrix(N_ROWS, N_COLS, ccm.words_for(N_ROWS, N_COLS, bc), dev)
+        self.pd = ccm.PackedMatrix(N_ROWS, N_COLS, ccm.words_for(N_ROWS, N_COLS, bd), dev)
+        self.py = ccm.PackedMatrix(N_ROWS, 1, ccm.words_for(N_ROWS, 1, by), dev)
         self.unp = torch.empty((N_ROWS, N_COLS), dtype=torch.int64, device=dev)
         self.got = torch.empty(GET_COUNT, dtype=torch.int64, device=dev)
         self.err = torch.zeros(2, dtype=torch.int32, device=dev)
@@ -144,6 +149,7 @@ class Workload:
         self.mc, self.md, self.my = self.pc.c(), self.pd.c(), self.py.c()
         self.profiled = ["pack", "unpack", "add", "scale", "matvec"]
         self.events = {k: [] for k in self.profiled}
+        self.call_events = {k: [] for k in self.profiled}
 
     def event_pair(self):
         """Two timing events whose CUDA handles exist already (torch creates
@@ -166,32 +172,48 @@ class Workload:
         by = ctypes.byref
 
         def prof(name):
+            # the main kernel of the next call (library hook) and the whole
+            # call (events on the stream before its first and after its last
+            # launch); the stream is backed up with queued steps, so the
+            # events see device time, not host gaps
             if profile:
                 e0, e1 = self.event_pair()
                 ccm.profile_next(e0, e1)
                 self.events[name].append((e0, e1))
+                c0, c1 = self.event_pair()
+                c0.record()
+                self.call_events[name].append((c0, c1))
+
+        def done(name):
+            if profile:
+                self.call_events[name][-1][1].record()
 
         rc = []
         prof("pack")
         vp = ctypes.c_void_p
         rc.append(L.ccm_pack(vp(A.data_ptr()), ccm.I64, N_ROWS, N_COLS, by(self.ma),
                              vp(self.ws_pa.data_ptr()), self.ws_pa.numel(), st))
+        done("pack")
         rc.append(L.ccm_pack(vp(B.data_ptr()), ccm.I64, N_ROWS, N_COLS, by(self.mb),
                              vp(self.ws_pb.data_ptr()), self.ws_pb.numel(), st))
         rc.append(L.ccm_pack(vp(X.data_ptr()), ccm.I64, N_COLS, 1, by(self.mx), None, 0, st))
         prof("unpack")
         rc.append(L.ccm_unpack(by(self.ma), ctypes.c_void_p(self.unp.data_ptr()), ccm.I64,
                                ctypes.c_void_p(self.err.data_ptr()), st))
+        done("unpack")
         rc.append(L.ccm_get(by(self.ma), ctypes.c_void_p(self.idx.data_ptr()), GET_COUNT,
                             ctypes.c_void_p(self.got.data_ptr()),
                             ctypes.c_void_p(self.err.data_ptr() + 4), st))
         prof("add")
         rc.append(L.ccm_add(by(self.ma), by(self.mb), by(self.mc), None, 0, st))
+        done("add")
         prof("scale")
         rc.append(L.ccm_scale(by(self.ma), SCALE, by(self.md), None, 0, st))
+        done("scale")
         prof("matvec")
         rc.append(L.ccm_matvec(by(self.ma), by(self.mx), by(self.my),
                                ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(), st))
+        done("matvec")
         if any(rc):
             raise RuntimeError(f"C ABI returned {rc}")
 
@@ -302,6 +324,8 @@ def run_gpu(args, rank, world, local_rank):
     # per-kernel times of the profiled main kernels
     kern_ms = {k: statistics.mean(e0.elapsed_time(e1) for e0, e1 in v)
                for k, v in wl.events.items() if v}
+    call_ms = {k: statistics.mean(e0.elapsed_time(e1) for e0, e1 in v)
+               for k, v in wl.call_events.items() if v}
     ops = wl.step_bytes()
     step_bytes = sum(ops.values())
     ms_per_step = ms / args.steps
@@ -322,6 +346,11 @@ def run_gpu(args, rank, world, local_rank):
         gbs = ops[k] / (t * 1e-3) / 1e9
         per_op[k] = {"kernel": kernels[k], "ms": round(t, 5), "algorithmic_bytes": int(ops[k]),
                      "GB/s": round(gbs, 1), "frac_of_hbm": round(gbs / hbm, 3)}
+        if k in call_ms:
+            # the whole call: every launch of the operation, epilogues included
+            gbc = ops[k] / (call_ms[k] * 1e-3) / 1e9
+            per_op[k].update({"ms_call": round(call_ms[k], 5), "GB/s_call": round(gbc, 1),
+                              "frac_of_hbm_call": round(gbc / hbm, 3)})
     def roofline(d):
         return {"bound": "hbm", "kernel": d["kernel"], "achieved": d["GB/s"], "peak": hbm,
                 "unit": "GB/s", "frac": round(d["GB/s"] / hbm, 4),
@@ -351,6 +380,9 @@ def run_gpu(args, rank, world, local_rank):
         "event_pair_floor_us": event_pair_floor(torch),
         "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
     }
+    # the metric's other two parts, measured in the same run (this rank's replica)
+    line["matmul"] = matmul_measure(torch, ccm, dev, args.matmul_n, SEED_A, reps=10)
+    line["batch"] = batch_measure(torch, ccm, dev, args.batch_count, SEED_A, steps=10, warmup=3)
     return line
 
 
@@ -366,20 +398,14 @@ def event_pair_floor(torch, reps: int = 50) -> float:
     return round(statistics.mean(ts), 2)
 
 
-def run_batch(args, rank, world, local_rank):
-    """Batched matvec workload: 10,000 packed matrices, rows/cols log-uniform in
+def batch_measure(torch, ccm, dev, count, seed, steps, warmup):
+    """Batched matvec: `count` packed matrices, rows/cols log-uniform in
     [16, 2048), widths uniform in 1..24, values uniform over the signed b-bit
     range, x signed 8-bit; one persistent graph-captured launch (autotuned)
-    against one ccm_matvec call per matrix on the same GPU."""
-    import torch
-
+    against one ccm_matvec call per matrix on the same GPU.  Per batch: the
+    mean over `steps` graph replays (inputs 2.7 GB, larger than L2)."""
     import synth
-    from paper_1303_0270_gb300 import ccm
     from paper_1303_0270_gb300.batch import BatchMatvec
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
-    count = args.batch_count
-    seed = SEED_A + 1000 * rank
     rows, cols, widths = synth.batch_shapes(seed, count)
     maxn = int((rows * cols).max())
     dense = torch.empty(maxn, dtype=torch.int64, device=dev)
@@ -399,30 +425,32 @@ def run_batch(args, rank, world, local_rank):
         mats.append(pa)
         xs.append(px)
         packed_bytes += ccm.words_for(r, c, b) * 4
+    del dense
     torch.cuda.synchronize()
     bm = BatchMatvec(mats, xs)
     tune = bm.autotune(reps=2)
     bm.capture()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         bm.run()
     torch.cuda.synchronize()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         bm.run()
     t1.record()
     torch.cuda.synchronize()
-    ms_batch = t0.elapsed_time(t1) / args.steps
+    ms_batch = t0.elapsed_time(t1) / steps
     # one launch sequence per matrix (ccm_matvec), same inputs
     ys = [ccm.PackedMatrix(m.rows, 1, bm.ys[i].capacity, dev) for i, m in enumerate(mats)]
     wss = torch.empty(ccm.workspace_bytes(ccm.OP_MATVEC, 2048, 2048, 1), dtype=torch.uint8,
                       device=dev)
+
     def plain():
         for a, x, y in zip(mats, xs, ys):
             ccm.matvec_into(a, x, y, ws=wss)
     plain()
     torch.cuda.synchronize()
-    reps = max(1, min(3, args.steps))
+    reps = max(1, min(3, steps))
     t0.record()
     for _ in range(reps):
         plain()
@@ -436,51 +464,57 @@ def run_batch(args, rank, world, local_rank):
             bad += 1
     hbm, _ = peaks()
     gbs = packed_bytes / (ms_batch * 1e-3) / 1e9
-    return {
-        "metric": METRIC, "workload": "batched matvec", "value": round(gbs, 2), "unit": "GB/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(ms_batch, 4), "higher_is_better": True, "scaling": "weak",
-        "dtype": "int64", "data": "synthetic",
-        "config": {"workload": f"{count} packed matrices, rows/cols log-uniform [16, 2048), "
-                               "widths U{1..24}, signed uniform values, x signed 8-bit",
-                   "packed_bytes": packed_bytes, "fields": int((rows * cols).sum()),
-                   "autotune": {k: tune[k] for k in ("unit_segments", "grid")}},
-        "frac_of_hbm": round(gbs / hbm, 4),
-        "plain_ms": round(ms_plain, 3), "speedup_vs_plain": round(ms_plain / ms_batch, 2),
-        "mismatches_vs_plain": bad,
-    }
+    return {"workload": f"{count} packed matrices, rows/cols log-uniform [16, 2048), "
+                        "widths U{1..24}, signed uniform values, x signed 8-bit",
+            "packed_bytes": packed_bytes, "fields": int((rows * cols).sum()),
+            "autotune": {k: tune[k] for k in ("unit_segments", "grid") if k in tune},
+            "ms": round(ms_batch, 4), "GB/s": round(gbs, 2), "frac_of_hbm": round(gbs / hbm, 4),
+            "plain_ms": round(ms_plain, 3), "speedup_vs_plain": round(ms_plain / ms_batch, 2),
+            "mismatches_vs_plain": bad, "timing": f"mean of {steps} graph replays, CUDA events"}
 
 
-def run_matmul_bench(args, rank, world, local_rank):
-    """Packed matmul: A, B 4096 x 4096 uniform over the signed b-bit range,
-    b in {4, 8, 12, 16}; exact int64 C re-packed at its width.  Tensor-core
-    digit path (tcgen05, e4m3 digits, fp32 accumulators) against the CUDA-core
-    decode-and-multiply path on the same inputs (results compared word for
-    word).  Useful ops = 2 * 4096^3 per matmul."""
+def run_batch(args, rank, world, local_rank):
     import torch
 
-    import synth
     from paper_1303_0270_gb300 import ccm
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    n = args.matmul_n
+    d = batch_measure(torch, ccm, dev, args.batch_count, SEED_A + 1000 * rank, args.steps,
+                      args.warmup)
+    return {
+        "metric": METRIC, "workload": "batched matvec", "value": d["GB/s"], "unit": "GB/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": d["ms"], "higher_is_better": True, "scaling": "weak",
+        "dtype": "int64", "data": "synthetic", "config": {"workload": d["workload"]},
+        "batch": d,
+    }
+
+
+def matmul_measure(torch, ccm, dev, n, seed_base, reps):
+    """Packed matmul: A, B n x n uniform over the signed b-bit range, b in
+    {4, 8, 12, 16}; exact int64 C re-packed at its width.  Tensor-core digit
+    path (tcgen05, e4m3 digits, fp32 accumulators) against the CUDA-core
+    decode-and-multiply path on the same inputs (results compared word for
+    word).  Useful ops = 2 n^3 per matmul; the whole call includes the digit
+    planes and C's re-pack."""
+    import synth
     peaks_d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     fp8_peak = 2.0 * float(peaks_d["bf16_tflops"])  # measured bf16 x nominal fp8/bf16 ratio (2)
     dense = torch.empty(n * n, dtype=torch.int64, device=dev)
+    ws = ccm.workspace(ccm.OP_MATMUL, n, n, n, dev)
     results = []
     for b in (4, 8, 12, 16):
         lo, hi = synth.signed_range(b)
-        seed = SEED_A + 1000 * rank + b
+        seed = seed_base + b
         ccm.gen_uniform(n * n, seed, synth.STREAM_A, lo, hi, out=dense)
         pa = ccm.pack_into(dense.view(n, n), ccm.PackedMatrix(n, n, ccm.words_for(n, n, b), dev))
         ccm.gen_uniform(n * n, seed, synth.STREAM_B, lo, hi, out=dense)
         pb = ccm.pack_into(dense.view(n, n), ccm.PackedMatrix(n, n, ccm.words_for(n, n, b), dev))
-        cap = ccm.words_for(n, n, min(64, 2 * b + 14))
-        ws = ccm.workspace(ccm.OP_MATMUL, n, n, n, dev)
+        cap = ccm.words_for(n, n, ccm.bound_matmul(pa, pb))
         ct = ccm.PackedMatrix(n, n, cap, dev)
         cc = ccm.PackedMatrix(n, n, cap, dev)
         timings = {}
-        for name, path, out, reps in (("tensor", ccm.MATMUL_TENSOR, ct, args.steps),
+        for name, path, out, nrep in (("tensor", ccm.MATMUL_TENSOR, ct, reps),
                                       ("cudacore", ccm.MATMUL_CUDACORE, cc, 2)):
             for _ in range(2):
                 ccm.matmul_into(pa, pb, out, path=path, ws=ws)
@@ -490,7 +524,7 @@ def run_matmul_bench(args, rank, world, local_rank):
             k0.record()
             k1.record()
             tot, kern = 0.0, 0.0
-            for _ in range(reps):
+            for _ in range(nrep):
                 ccm.profile_next(k0, k1)
                 e0.record()
                 ccm.matmul_into(pa, pb, out, path=path, ws=ws)
@@ -498,7 +532,7 @@ def run_matmul_bench(args, rank, world, local_rank):
                 e1.synchronize()
                 tot += e0.elapsed_time(e1)
                 kern += k0.elapsed_time(k1)
-            timings[name] = (tot / reps, kern / reps)
+            timings[name] = (tot / nrep, kern / nrep)
         same = (ct.check().width == cc.check().width and torch.equal(ct.words(), cc.words()))
         L = (b + 3) // 4
         useful = 2.0 * n ** 3
@@ -513,6 +547,8 @@ def run_matmul_bench(args, rank, world, local_rank):
             "cudacore_useful_int_TOPS": round(useful / (timings["cudacore"][0] * 1e-3) / 1e12, 3),
             "speedup_tensor_vs_cudacore": round(timings["cudacore"][0] / t_all, 2),
         })
+        del pa, pb, ct, cc
+    del dense, ws
     # reference point: a plain s8 x s8 -> s32 GEMM of the same size through
     # the vendor library (torch._int_mm -> cuBLASLt), the integer tensor rate
     # an int8-limb design would get on this GPU
@@ -532,13 +568,25 @@ def run_matmul_bench(args, rank, world, local_rank):
         int8_tops = round(2.0 * n ** 3 / (e0.elapsed_time(e1) / 10 * 1e-3) / 1e12, 1)
     except RuntimeError:
         pass
-    return {"metric": METRIC, "workload": "packed matmul", "unit": "int-TOPS (useful)",
-            "value": round(statistics.mean(r["useful_int_TOPS"] for r in results), 2),
-            "n": n, "fp8_peak_TFLOPS": fp8_peak,
+    return {"n": n, "unit": "int-TOPS (useful)",
+            "useful_int_TOPS_mean": round(statistics.mean(r["useful_int_TOPS"] for r in results), 2),
+            "fp8_peak_TFLOPS": fp8_peak,
             "fp8_peak_source": "MEASURED_PEAKS bf16_tflops x 2 (nominal fp8/bf16 ratio)",
             "s8_gemm_library_TOPS": int8_tops,
             "s8_gemm_library": "torch._int_mm (cuBLASLt) s8 x s8 -> s32, same n, 10 launches",
+            "timing": f"whole call and MMA kernel, mean of {reps} calls, CUDA events",
             "results": results}
+
+
+def run_matmul_bench(args, rank, world, local_rank):
+    import torch
+
+    from paper_1303_0270_gb300 import ccm
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    d = matmul_measure(torch, ccm, dev, args.matmul_n, SEED_A + 1000 * rank, args.steps)
+    return {"metric": METRIC, "workload": "packed matmul", "unit": d["unit"],
+            "value": d["useful_int_TOPS_mean"], "matmul": d}
 
 
 def run_vlb_bench(args, rank, world, local_rank):

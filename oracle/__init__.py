@@ -222,6 +222,25 @@ def matmul_dense(a, b, rows=None) -> np.ndarray:
     return c
 
 
+def matmul_dense_f64(a, b) -> np.ndarray:
+    """The same integer product C = A B (Introduction: the compressed form
+    supports the same mathematics), with a float64 BLAS matrix product as the
+    one library step.  Exact when max|a| * max|b| * k < 2^53: every product
+    and every partial sum, in whatever order the library adds them, is then
+    an integer that float64 represents exactly.  Raises ValueError outside
+    that range (use matmul_dense there)."""
+    a, b = _i64(a), _i64(b)
+    m, k = a.shape
+    k2, n = b.shape
+    assert k == k2
+    ma = int(np.abs(a).max()) if a.size else 0
+    mb = int(np.abs(b).max()) if b.size else 0
+    if ma * mb * max(k, 1) >= 1 << 53:
+        raise ValueError("float64 product not exact for these magnitudes")
+    c = np.matmul(a.astype(np.float64), b.astype(np.float64))
+    return c.astype(np.int64)
+
+
 # Operations on the compressed form: unpack, operate, re-pack at the new width.
 def add(pa: Packed, pb: Packed) -> Packed:
     assert (pa.rows, pa.cols) == (pb.rows, pb.cols)

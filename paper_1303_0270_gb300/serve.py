@@ -37,6 +37,7 @@ class Request:
     done: float = -1.0
     event: object = None
     nbytes: int = 0
+    recipe: tuple = None      # pack: how `dense` was generated (seed, stream, lo, hi)
 
 
 @dataclass
@@ -242,6 +243,8 @@ def build_store(seed: int, target_bytes: int, lo: int, hi: int, wlo: int, whi: i
                         out=dense[: r * c])
         m = ccm.PackedMatrix(r, c, ccm.words_for(r, c, b), device)
         ccm.pack_into(dense[: r * c].view(r, c), m)
+        # the generator inputs of this matrix (entries uniform in [lo, hi])
+        m.recipe = (synth.batch_matrix_seed(seed, i), synth.STREAM_A, lo_v, hi_v)
         store.append(m)
         total += nbytes
     torch.cuda.synchronize(device)
@@ -249,12 +252,14 @@ def build_store(seed: int, target_bytes: int, lo: int, hi: int, wlo: int, whi: i
 
 
 def build_trace(seed: int, store, count: int, rate: float, device, mix=(0.6, 0.3, 0.1),
-                pack_sizes=(64, 1024), matmul_max_dim: int = 2048):
+                pack_sizes=(64, 8192), matmul_max_dim: int = 8192):
     """`count` requests with Poisson(rate) arrivals (rate = inf: all at t = 0)
     mixing matvec / pack / matmul in the proportions `mix`.  Matvec uses a
     packed signed 8-bit x per store matrix; pack draws a dense matrix
     (dims log-uniform in pack_sizes) from a pool; matmul multiplies consecutive
-    store matrices A_i A_{i+1} whose dims are at most matmul_max_dim."""
+    store matrices A_i A_{i+1} whose dims are at most matmul_max_dim.  Each
+    x (attribute `recipe`) and each pack request (`Request.recipe`) records
+    the generator inputs of its entries."""
     import numpy as np
 
     import synth
@@ -269,15 +274,17 @@ def build_trace(seed: int, store, count: int, rate: float, device, mix=(0.6, 0.3
         if m.cols not in xs:
             ccm.gen_uniform(m.cols, seed + i, synth.STREAM_X, -128, 127, out=xd[: m.cols])
             xs[m.cols] = ccm.pack(xd[: m.cols].view(-1, 1).clone())
+            xs[m.cols].recipe = (seed + i, synth.STREAM_X, -128, 127)
     mm_ok = [i for i in range(len(store) - 1)
              if max(store[i].rows, store[i].cols, store[i + 1].cols) <= matmul_max_dim]
     pdims = synth.log_uniform_sizes(seed + 7, synth.STREAM_SHAPES, 16, pack_sizes[0], pack_sizes[1])
-    pool = []
+    pool, recipes = [], []
     for j in range(8):
         r, c = int(pdims[2 * j]), int(pdims[2 * j + 1])
         d = torch.empty(r * c, dtype=torch.int64, device=device)
         ccm.gen_uniform(r * c, seed + 100 + j, synth.STREAM_A, -(1 << 11), (1 << 11) - 1, out=d)
         pool.append(d.view(r, c))
+        recipes.append((seed + 100 + j, synth.STREAM_A, -(1 << 11), (1 << 11) - 1))
     trace = []
     for k in range(count):
         p = int(pick[k])
@@ -285,7 +292,8 @@ def build_trace(seed: int, store, count: int, rate: float, device, mix=(0.6, 0.3
             a = p % len(store)
             trace.append(Request(k, "matvec", float(arrivals[k]), a=a, x=xs[store[a].cols]))
         elif kinds_u[k] < mix[0] + mix[1]:
-            trace.append(Request(k, "pack", float(arrivals[k]), dense=pool[p % len(pool)]))
+            trace.append(Request(k, "pack", float(arrivals[k]), dense=pool[p % len(pool)],
+                                 recipe=recipes[p % len(pool)]))
         else:
             i = mm_ok[p % len(mm_ok)]
             trace.append(Request(k, "matmul", float(arrivals[k]), a=i, b=i + 1))

@@ -63,10 +63,11 @@ def test_width_sweep(ccm, b):
     pa, pb, px = ccm.pack(to_dev(a)), ccm.pack(to_dev(bb)), ccm.pack(to_dev(x))
     assert_same_packed(pa, oa, f"sweep pack b={b}")
     assert np.array_equal(ccm.unpack(pa).cpu().numpy(), a)
-    c = ccm.unpack(ccm.add(pa, pb).check()).cpu().numpy()
-    assert np.array_equal(c, a + bb)
-    d = ccm.unpack(ccm.scale(pa, -7).check()).cpu().numpy()
-    assert np.array_equal(d, a * -7)
+    ob = oracle.pack(bb)
+    # packed words, width, sign mode and padding of C against the oracle
+    assert_same_packed(ccm.add(pa, pb), oracle.add(oa, ob), f"sweep add b={b}")
+    assert_same_packed(ccm.scale(pa, -7), oracle.scale(oa, -7), f"sweep scale -7 b={b}")
+    assert_same_packed(ccm.scale(pa, 7), oracle.scale(oa, 7), f"sweep scale 7 b={b}")
     y = ccm.unpack(ccm.matvec(pa, px).check()).cpu().numpy().ravel()
     sample = np.unique(synth.uniform_int(b, synth.STREAM_INDEX, 64, 0, rows - 1))
     assert np.array_equal(y[sample], oracle.matvec_dense(a, x.ravel(), rows=sample))
@@ -74,20 +75,28 @@ def test_width_sweep(ccm, b):
 
 @pytest.mark.parametrize("b", [4, 8, 12, 16])
 def test_matmul_4096(ccm, b):
+    """4096^3 at b in {4, 8, 12, 16}: the tensor path's whole packed C (every
+    word, exact width, sign mode, padding) equals the CUDA-core path's and the
+    oracle's.  The oracle's product is the float64 BLAS one, exact here since
+    |a| |b| k <= 2^15 * 2^15 * 2^12 < 2^53."""
     n = 4096
     dev = device()
     lo, hi = synth.signed_range(b)
     A = ccm.gen_uniform(n * n, 1303 + b, synth.STREAM_A, lo, hi, device=dev).view(n, n)
     B = ccm.gen_uniform(n * n, 1303 + b, synth.STREAM_B, lo, hi, device=dev).view(n, n)
+    a = synth.uniform_signed(1303 + b, synth.STREAM_A, n * n, b).reshape(n, n)
+    bm = synth.uniform_signed(1303 + b, synth.STREAM_B, n * n, b).reshape(n, n)
+    assert np.array_equal(A.cpu().numpy(), a) and np.array_equal(B.cpu().numpy(), bm)
     pa, pb = ccm.pack(A), ccm.pack(B)
-    c = ccm.matmul(pa, pb, path=ccm.MATMUL_TENSOR).check()
-    rows = [0, 1, 2047, 4095]
-    a_rows = A[rows].cpu().numpy()
-    expect = oracle.matmul_dense(a_rows, B.cpu().numpy())
-    got = ccm.unpack(c).cpu().numpy()[rows]
-    assert np.array_equal(got, expect)
-    # the exact width of C from the sampled rows can only be smaller
-    assert c.width >= oracle.width(expect)[0]
+    del A, B
+    ct = ccm.matmul(pa, pb, path=ccm.MATMUL_TENSOR)
+    cc = ccm.matmul(pa, pb, path=ccm.MATMUL_CUDACORE, capacity=ct.capacity)
+    expect = oracle.pack(oracle.matmul_dense_f64(a, bm))
+    assert_same_packed(ct, expect, f"4096^3 tensor b={b}")
+    assert_same_packed(cc, expect, f"4096^3 CUDA-core b={b}")
+    # and the int64 product rows by the plain oracle loop
+    rows = [0, 2047, 4095]
+    assert np.array_equal(oracle.matmul_dense(a[rows], bm), oracle.unpack(expect)[rows])
 
 
 def test_batch_10000(ccm):

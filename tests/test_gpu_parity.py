@@ -515,6 +515,34 @@ def test_matmul_tensor_worst_case_sums(ccm):
     assert np.array_equal(got[rows], expect)
 
 
+def test_matmul_tensor_class_sums_cross_2_23(ccm):
+    """Mixed-sign digits whose class sums rise above 2^23 within K and come
+    back down: P = 32767 has digits (15, 15, 15, 7), N = -32753 has digits
+    (15, 0, 0, -8).  For an even row times an even column the middle class
+    gains 660 per step over the first 13,000 steps (8.58e6 > 2^23) and then
+    loses 240 per step over the last 5,000; the fp32 accumulators are exact
+    for every integer below 2^24 (k * 4 * 225 < 2^24 at k = 18,000), so the
+    products must come out exact.  A sprinkle of random entries breaks the
+    symmetry."""
+    k1, k2 = 13000, 5000
+    k = k1 + k2
+    P, N = 32767, -32753
+    a = np.empty((128, k), dtype=np.int64)
+    a[0::2, :k1], a[0::2, k1:] = P, N
+    a[1::2, :k2], a[1::2, k2:] = N, P
+    bm = np.empty((k, 64), dtype=np.int64)
+    bm[:k1, 0::2], bm[k1:, 0::2] = P, N
+    bm[:k2, 1::2], bm[k2:, 1::2] = N, P
+    noise_a = _rand(41, (128, k), 16)
+    noise_b = _rand(42, (k, 64), 16)
+    a[:, ::97] = noise_a[:, ::97]
+    bm[::89, :] = noise_b[::89, :]
+    expect = oracle.pack(oracle.matmul_dense(a, bm))
+    pa, pb = _pack_cap(ccm, a, 16), _pack_cap(ccm, bm, 16)
+    c = ccm.matmul(pa, pb, path=ccm.MATMUL_TENSOR, capacity=ccm.words_for(128, 64, 64))
+    assert_same_packed(c, expect, "tensor matmul, class sums across 2^23")
+
+
 def test_matmul_tensor_and_cudacore_agree(ccm):
     m, k, n = 384, 1000, 272
     for b in (4, 8, 13, 16):

@@ -177,3 +177,30 @@ def test_matvec_chain_associates():
     ab_x = oracle.matvec(oracle.matmul(oracle.pack(a), oracle.pack(b)), oracle.pack(x))
     assert (ab_x.width, ab_x.is_signed) == (chain.width, chain.is_signed)
     assert np.array_equal(ab_x.words, chain.words)
+
+
+@pytest.mark.parametrize("m,k,n,b", [(1, 1, 1, 1), (9, 17, 6, 8), (33, 40, 31, 16), (5, 300, 7, 20)])
+def test_matmul_f64_textbook(m, k, n, b):
+    """The float64-BLAS product equals textbook Python-integer loops."""
+    rng = np.random.default_rng(7 * m + k + n + b)
+    a, bm = _rand(rng, (m, k), b), _rand(rng, (k, n), b)
+    assert np.array_equal(oracle.matmul_dense_f64(a, bm),
+                          np.array(_py_matmul(a, bm), dtype=np.int64))
+
+
+def test_matmul_f64_near_its_exactness_limit():
+    """Sums just below 2^53 in magnitude, reached through partial sums of
+    both signs, stay exact; at the limit the function refuses."""
+    k = 8
+    big = (1 << 22) - 1  # |a| * |b| * k = (2^22-1)^2 * 8 < 2^47
+    a = np.full((3, k), big, dtype=np.int64)
+    a[1, ::2] = -big
+    b = np.full((k, 2), big, dtype=np.int64)
+    assert np.array_equal(oracle.matmul_dense_f64(a, b), np.array(_py_matmul(a, b), dtype=np.int64))
+    x = (1 << 24) + 1  # odd, so products need every bit
+    a2 = np.array([[x, -x, x]], dtype=np.int64)
+    b2 = np.array([[x], [x], [x + 2]], dtype=np.int64)
+    assert int(oracle.matmul_dense_f64(a2, b2)[0, 0]) == x * x - x * x + x * (x + 2)
+    with pytest.raises(ValueError):
+        oracle.matmul_dense_f64(np.full((1, 2), 1 << 26, dtype=np.int64),
+                                np.full((2, 1), 1 << 26, dtype=np.int64))
