@@ -161,7 +161,7 @@ class Workload:
             pair.append(e)
         return pair
 
-    def step(self, profile: bool = False, A=None, B=None, X=None):
+    def step(self, profile: str = "", A=None, B=None, X=None):
         """One pass of the hot path through the C ABI (asynchronous)."""
         import ctypes
         ccm, L = self.ccm, self.ccm.lib()
@@ -171,21 +171,24 @@ class Workload:
         X = self.X if X is None else X
         by = ctypes.byref
 
+        # profile == "call": events on the stream before the first and after
+        # the last launch of each profiled call (the stream is backed up with
+        # queued steps, so they see device time, not host gaps).
+        # profile == "kernel": the library hook brackets each call's main
+        # kernel (that call then launches without programmatic dependent
+        # launch, so the timed steps use "call" only).
         def prof(name):
-            # the main kernel of the next call (library hook) and the whole
-            # call (events on the stream before its first and after its last
-            # launch); the stream is backed up with queued steps, so the
-            # events see device time, not host gaps
-            if profile:
+            if profile == "kernel":
                 e0, e1 = self.event_pair()
                 ccm.profile_next(e0, e1)
                 self.events[name].append((e0, e1))
+            elif profile == "call":
                 c0, c1 = self.event_pair()
                 c0.record()
                 self.call_events[name].append((c0, c1))
 
         def done(name):
-            if profile:
+            if profile == "call":
                 self.call_events[name][-1][1].record()
 
         rc = []
@@ -309,12 +312,16 @@ def run_gpu(args, rank, world, local_rank):
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record()
     for _ in range(args.steps):
-        wl.step(profile=True)
+        wl.step(profile="call")
     t1.record()
     barrier()
     launches = ccm.launch_count() - launches0
     ms = t0.elapsed_time(t1)
     clocks = sampler.stop() if rank == 0 else None
+    # main-kernel times: the same steps again, each op's main kernel bracketed
+    for _ in range(args.steps):
+        wl.step(profile="kernel")
+    torch.cuda.synchronize()
     if dist is not None:
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)

@@ -18,6 +18,10 @@ int bitlen_host(uint64_t v);
 // Launch accounting and the per-call profiling hook (ccm_profile_next).
 void note_launch(int count = 1);
 void profile_begin(cudaStream_t st);
+// True when the next profile_begin() will record (the calling thread armed
+// ccm_profile_next); such a call launches without programmatic dependent
+// launch, so no event record sits between two programmatically linked kernels.
+bool profile_armed();
 void profile_end(cudaStream_t st);
 
 void run_measure(const void* dense, int dtype, uint64_t rows, uint64_t cols, ccm_header* hdr,
@@ -42,6 +46,13 @@ void run_pack_scratch(const int64_t* vals, const ccm_matrix& out, cudaStream_t s
 // shapes, y's minimum capacity).
 ccm_status matvec_host_check(const ccm_matrix* a, const ccm_matrix* x, const ccm_matrix* y);
 size_t matvec_workspace(uint64_t m, uint64_t n);
+// The streaming matvec (matvec_stream.cu): whether it takes an m x n product
+// whose widths the capacities bound by bmax_a and bmax_x, and its launches.
+namespace mvs {
+bool stream_applies(uint64_t m, uint64_t n, int bmax_a, int bmax_x);
+void run_stream(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& y, void* ws,
+                cudaStream_t st);
+}  // namespace mvs
 size_t matvec2_workspace(uint64_t m, uint64_t n1, uint64_t n2);
 void run_matvec2(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& b,
                  const ccm_matrix& z, const ccm_matrix& y, void* ws, cudaStream_t st);

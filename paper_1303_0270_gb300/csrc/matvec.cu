@@ -318,6 +318,12 @@ InitArgs matvec_init(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix&
 
 void run_matvec(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& y, void* ws,
                 cudaStream_t st) {
+  const uint64_t n_a = a.rows * a.cols;
+  if (mvs::stream_applies(a.rows, a.cols, width_bound(a.capacity, n_a),
+                          width_bound(x.capacity, a.cols))) {
+    mvs::run_stream(a, x, y, ws, st);
+    return;
+  }
   auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
   int64_t* xs = (int64_t*)ws;
   int64_t* yv = (int64_t*)((char*)ws + up(a.cols * sizeof(int64_t)));

@@ -20,6 +20,8 @@ void profile_begin(cudaStream_t st) {
   }
 }
 
+bool profile_armed() { return t_armed && !t_open; }
+
 void profile_end(cudaStream_t st) {
   if (t_armed && t_open) {
     cudaEventRecord(t_stop, st);
