@@ -104,17 +104,43 @@ __device__ __forceinline__ int64_t decode_field(const uint32_t* __restrict__ w, 
   return extend(bits, b, sgn);
 }
 
+// The first 32 bytes of a header (magic, width, sign, status, rows, cols),
+// read with two 16-byte loads issued together: one memory round trip.
+struct HeaderView {
+  uint32_t magic;
+  int width, is_signed, status;
+  uint64_t rows, cols;
+};
+
+__device__ __forceinline__ HeaderView load_header(const ccm_header* h) {
+  const uint4* p = reinterpret_cast<const uint4*>(h);
+  const uint4 q0 = p[0], q1 = p[1];
+  HeaderView v;
+  v.magic = q0.x;
+  v.width = (int)q0.y;
+  v.is_signed = (int)q0.z;
+  v.status = (int)q0.w;
+  v.rows = ((uint64_t)q1.y << 32) | q1.x;
+  v.cols = ((uint64_t)q1.w << 32) | q1.z;
+  return v;
+}
+
 // A valid input header: magic set, no error, width in range, the expected
 // shape, and words that fit the caller's buffer (so no read can leave it).
 // Returns CCM_OK or the status to pass on.
+__device__ __forceinline__ int check_header(const HeaderView& h, uint64_t rows, uint64_t cols,
+                                            uint64_t capacity) {
+  if (h.magic != CCM_MAGIC) return CCM_E_INPUT;
+  if (h.status != CCM_OK) return h.status;
+  if (h.width < 1 || h.width > 64) return CCM_E_INPUT;
+  if (h.rows != rows || h.cols != cols) return CCM_E_INPUT;
+  if (words_for(rows * cols, h.width) > capacity) return CCM_E_INPUT;
+  return CCM_OK;
+}
+
 __device__ __forceinline__ int check_input(const ccm_header* h, uint64_t rows, uint64_t cols,
                                            uint64_t capacity) {
-  if (h->magic != CCM_MAGIC) return CCM_E_INPUT;
-  if (h->status != CCM_OK) return h->status;
-  if (h->width < 1 || h->width > 64) return CCM_E_INPUT;
-  if (h->rows != rows || h->cols != cols) return CCM_E_INPUT;
-  if (words_for(rows * cols, h->width) > capacity) return CCM_E_INPUT;
-  return CCM_OK;
+  return check_header(load_header(h), rows, cols, capacity);
 }
 
 __device__ __forceinline__ void set_status(ccm_header* h, int code) {

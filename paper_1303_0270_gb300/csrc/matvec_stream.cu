@@ -1,6 +1,7 @@
 // matvec_stream.cu -- the launch chain of the streaming matvec (see
 // matvec_stream.cuh): k_mv_init, k_mv, k_mv_ypack, the last two started by
 // programmatic dependent launch.
+#include <map>
 #include <mutex>
 
 #include "kernels.h"
@@ -11,18 +12,19 @@ namespace ccm {
 namespace mvs {
 namespace {
 
-constexpr int kInitThreads = 128;  // one x chunk (128 fields) per CTA pass
+constexpr int kInitThreads = 256;
 constexpr int kYThreads = 1024;
 
-// Validates A and x, clears y's header and the int64 sums, and decodes x
-// into the image k_mv copies to shared memory: per 128-column chunk c, x in
-// the byte order of dp4a_stage (b <= 8 and b_x <= 8) or as int32, then one
-// int per chunk, the sum of its x (the offset-binary correction).
-__global__ void __launch_bounds__(kInitThreads) k_mv_init(Args a, uint8_t* ximg) {
-  ax::grid_dep_launch();  // k_mv may start issuing its copies of A now
-  __shared__ int s_part[kInitThreads / 32];
-  int st = check_input(a.ha, a.m, a.n, a.a_cap);
-  if (st == CCM_OK) st = check_input(a.hx, a.n, 1, a.x_cap);
+// Validates A and x (the status goes into y's header), initialises y's
+// header, clears the int64 sums and decodes x into the image k_mv reads: per
+// 128-column chunk c, x in the byte order of the byte-lane decode (dp) or as
+// int32, then one int per chunk, the sum of its x (the offset-binary
+// correction).  Warp w of CTA k takes chunk 8k + w (lane l: fields 4l..4l+3).
+__global__ void __launch_bounds__(kInitThreads) k_mv_init(Args a) {
+  ax::grid_dep_launch();  // k_mv may start streaming A now
+  const HeaderView ha = load_header(a.ha), hx = load_header(a.hx);
+  int st = check_header(ha, a.m, a.n, a.a_cap);
+  if (st == CCM_OK) st = check_header(hx, a.n, 1, a.x_cap);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ccm_header* o = a.out;
     o->magic = CCM_MAGIC;
@@ -41,46 +43,63 @@ __global__ void __launch_bounds__(kInitThreads) k_mv_init(Args a, uint8_t* ximg)
   for (uint64_t i = (uint64_t)blockIdx.x * kInitThreads + threadIdx.x; i < a.m; i += stride)
     a.y[i] = 0;
   if (st != CCM_OK) return;
-  const int b = a.ha->width, bx = a.hx->width, sx = a.hx->is_signed;
-  if (!stream_ok(b, bx, a.n)) return;  // k_mv reports it
-  const bool dp = b <= 8 && bx <= 8;
+  const int b = ha.width, bx = hx.width, sx = hx.is_signed;
+  if (!stream_ok(b, bx, a.n) || (a.dp && bx > 8)) return;  // k_mv reports it
+  const bool dp = a.dp != 0;
   const uint32_t nchunks = (uint32_t)(a.n / kKC);
-  int* csum = reinterpret_cast<int*>(ximg + (uint64_t)nchunks * (dp ? kXPitch8 : kXPitch32));
-  const uint32_t f = threadIdx.x;
-  for (uint32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-    const int v = (int)decode_field(a.wx, (uint64_t)c * kKC + f, bx, sx);
-    if (dp)
-      ximg[(uint64_t)c * kXPitch8 + mvf::rows::x8_pos_rt(f, b)] = (uint8_t)v;
-    else
-      reinterpret_cast<int*>(ximg + (uint64_t)c * kXPitch32)[f] = v;
-    int sum = v;
-    for (int d = 16; d; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
-    if (f % 32 == 0) s_part[f / 32] = sum;
-    __syncthreads();
-    if (f == 0) csum[c] = s_part[0] + s_part[1] + s_part[2] + s_part[3];
-    __syncthreads();
+  int* csum = reinterpret_cast<int*>(a.ximg + (uint64_t)nchunks * (dp ? kXPitch8 : kXPitch32));
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  for (uint32_t c = blockIdx.x * (kInitThreads / 32) + warp; c < nchunks;
+       c += gridDim.x * (kInitThreads / 32)) {
+    int v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      v[q] = (int)decode_field(a.wx, (uint64_t)c * kKC + 4 * lane + q, bx, sx);
+    if (dp) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        a.ximg[(uint64_t)c * kXPitch8 + mvf::rows::x8_pos_rt(4 * lane + q, b)] = (uint8_t)v[q];
+    } else {
+      reinterpret_cast<int4*>(a.ximg + (uint64_t)c * kXPitch32)[lane] =
+          make_int4(v[0], v[1], v[2], v[3]);
+    }
+    const int sum = __reduce_add_sync(0xffffffffu, v[0] + v[1] + v[2] + v[3]);
+    if (lane == 0) csum[c] = sum;
   }
 }
 
 // y's width (statistics of the int64 sums), header, and y packed at that
-// width, by one CTA: every sum is read once into shared memory, then each
-// thread assembles whole words of the stream from the fields that overlap
-// them (no word is written twice).
+// width, by one CTA.  The sums are read once into shared memory, 33 slots per
+// 32-field group; a 32-field group is b whole words, and lane i of the warp
+// that takes the group assembles its words i and i + 32 from the fields that
+// overlap them (no word is written twice).
 __global__ void __launch_bounds__(kYThreads) k_mv_ypack(ccm_header* out, uint32_t* words,
-                                                        uint64_t capacity, const int64_t* y,
+                                                        uint64_t capacity,
+                                                        const int64_t* __restrict__ y,
                                                         uint64_t m) {
   extern __shared__ uint64_t ys[];
   __shared__ uint64_t s_or[kYThreads / 32];
   __shared__ uint32_t s_neg[kYThreads / 32];
   ax::grid_dep_wait();  // every sum of k_mv is in place
   if (out->status != CCM_OK) return;
+  const uint32_t mm = (uint32_t)m;  // <= kYSmallRows
   uint64_t orv = 0;
   uint32_t neg = 0;
-  for (uint64_t i = threadIdx.x; i < m; i += kYThreads) {
-    const int64_t v = y[i];
-    ys[i] = (uint64_t)v;
-    orv |= fold(v);
-    neg |= (uint32_t)(v < 0);
+  // loads in batches of 8 per thread, all in flight together
+  for (uint32_t base = 0; base < mm; base += 8 * kYThreads) {
+    int64_t v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint32_t i = base + j * kYThreads + threadIdx.x;
+      v[j] = i < mm ? y[i] : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint32_t i = base + j * kYThreads + threadIdx.x;
+      if (i < mm) ys[(i >> 5) * 33 + (i & 31)] = (uint64_t)v[j];
+      orv |= fold(v[j]);
+      neg |= (uint32_t)(v[j] < 0);
+    }
   }
   orv = warp_or64(orv);
   neg = __reduce_or_sync(0xffffffffu, neg);
@@ -108,38 +127,64 @@ __global__ void __launch_bounds__(kYThreads) k_mv_ypack(ccm_header* out, uint32_
     if (nw > capacity) out->status = CCM_E_CAPACITY;
   }
   if (nw > capacity) return;
+  // group g (32 fields = b words) to warp g mod 32: lane i assembles words
+  // i and i + 32 of the group from the fields that overlap them
   const uint64_t mask = field_mask(b);
-  for (uint64_t W = threadIdx.x; W < nw; W += kYThreads) {
-    uint32_t acc = 0;
-    if (W < dw) {
-      const uint64_t bit0 = W * 32;
-      uint64_t f = bit0 / (uint64_t)b;
-      const uint64_t f_end = umin((bit0 + 31) / (uint64_t)b, m - 1);
-      for (; f <= f_end; ++f) {
-        const int64_t o = (int64_t)(f * (uint64_t)b) - (int64_t)bit0;  // field start in the word
-        const uint64_t pat = ys[f] & mask;
+  const uint32_t groups = (mm + 31) / 32;
+  int flo[2], fhi[2];  // fields overlapping word i (and i + 32) of a group
+  for (int h = 0; h < 2; ++h) {
+    const int wi = lane + 32 * h;
+    flo[h] = wi * 32 / b;
+    fhi[h] = (wi * 32 + 31) / b;
+  }
+  for (uint32_t g = warp; g < groups; g += kYThreads / 32) {
+    const uint32_t nf = umin(32, mm - g * 32);
+    const uint32_t nwg = (uint32_t)((nf * (uint64_t)b + 31) / 32);  // words of this group
+    const uint64_t* src = ys + g * 33;
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t wi = lane + 32 * h;
+      if (wi >= nwg) continue;
+      uint32_t acc = 0;
+      const int fe = fhi[h] < (int)nf - 1 ? fhi[h] : (int)nf - 1;
+      for (int f = flo[h]; f <= fe; ++f) {
+        const int o = f * b - (int)wi * 32;  // field start relative to the word
+        const uint64_t pat = src[f] & mask;
         acc |= o >= 0 ? (uint32_t)(pat << o) : (uint32_t)(pat >> (-o));
       }
+      words[(uint64_t)g * b + wi] = acc;
     }
-    words[W] = acc;
   }
+  // the zero pad words after the data words
+  for (uint64_t W = dw + threadIdx.x; W < nw; W += kYThreads) words[W] = 0;
 }
 
 std::mutex g_attr_mutex;
 int g_attr_dev = -1;
+std::map<uint64_t, std::pair<int, int>> g_plans;  // (device, widths, path) -> (ring depth, CTAs per SM)
+size_t g_dyn_max = 0;  // dynamic shared memory k_mv may use (opt-in minus its static share)
 
-// Opt-in shared memory for k_mv and k_mv_ypack on the current device (once).
-void set_attrs() {
+// Opt-in shared memory for k_mv and k_mv_ypack on the current device (once):
+// the largest dynamic size is the opt-in limit minus the kernel's static
+// shared memory.
+size_t set_attrs() {
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lock(g_attr_mutex);
-  if (g_attr_dev == dev) return;
-  const int cap = max_smem_optin();
-  cudaFuncSetAttribute(k_mv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_mv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  if (g_attr_dev == dev) return g_dyn_max;
+  const size_t cap = (size_t)max_smem_optin();
+  size_t dyn = cap;
+  const auto fns = {k_mv<true, true>, k_mv<true, false>, k_mv<false, true>, k_mv<false, false>};
+  for (auto fn : fns) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess && fa.sharedSizeBytes < cap)
+      dyn = umin(dyn, cap - fa.sharedSizeBytes);
+  }
+  for (auto fn : fns) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   cudaFuncSetAttribute(k_mv_ypack, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)(kYSmallRows * 8));
+                       (int)(kYSmallRows / 32 * 33 * 8));
+  g_dyn_max = dyn;
   g_attr_dev = dev;
+  return dyn;
 }
 
 }  // namespace
@@ -147,62 +192,75 @@ void set_attrs() {
 bool stream_applies(uint64_t m, uint64_t n, int bmax_a, int bmax_x) {
   if (!m || !n || n % kKC) return false;
   if (bmax_a > 8 || bmax_x > 31 || bmax_a + bmax_x + bitlen_host(n) > 63) return false;
-  const bool bytes = bmax_x <= 8;
-  const uint64_t xb = (x_image_bytes(n, bytes) + 15) & ~(uint64_t)15;
-  // two slots per warp beside the x image
-  return (uint64_t)kWarps * 2 * slot_bytes(bmax_a) + xb + 1024 <= (uint64_t)max_smem_optin();
+  // two slots per warp
+  return (uint64_t)kWarps * 2 * slot_bytes(bmax_a) <= (uint64_t)set_attrs();
 }
 
 void run_stream(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& y, void* ws,
                 cudaStream_t st) {
   const uint64_t m = a.rows, n = a.cols;
   const int bmax_a = width_bound(a.capacity, m * n), bmax_x = width_bound(x.capacity, n);
-  set_attrs();
+  const size_t dyn_max = set_attrs();
   auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
-  uint8_t* ximg = reinterpret_cast<uint8_t*>(ws);
+  uint8_t* ximg = reinterpret_cast<uint8_t*>(ws);  // x image: <= 4.2 n bytes of the 8 n
   int64_t* yv = reinterpret_cast<int64_t*>((char*)ws + up(n * sizeof(int64_t)));
-  const bool bytes = bmax_x <= 8;
-  const uint32_t xbytes = (uint32_t)((x_image_bytes(n, bytes) + 15) & ~(uint64_t)15);
   const bool narrow = bmax_a + bmax_x + 7 <= 31;
+  const bool dp = bmax_x <= 8;
+  auto kmv = dp ? (narrow ? k_mv<true, true> : k_mv<true, false>)
+                : (narrow ? k_mv<false, true> : k_mv<false, false>);
   // ring depth: the most resident warps, then the most bytes in flight
+  // (planned once per device, widths and path; the occupancy queries are
+  // slow next to a launch)
   const uint32_t sb = slot_bytes(bmax_a);
   const uint64_t nchunks = n / kKC;
   const uint64_t T = m * ((nchunks + kChunks - 1) / kChunks);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const uint64_t key = ((uint64_t)dev << 32) | ((uint64_t)bmax_a << 16) | ((uint64_t)dp << 8) |
+                       (uint64_t)narrow;
   int best_d = 0, best_per_sm = 0;
-  uint64_t best_warps = 0, best_flight = 0;
-  for (int d : {4, 3, 2}) {
-    const size_t smem = (size_t)kWarps * d * sb + xbytes;
-    if (smem > (size_t)max_smem_optin()) continue;
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, narrow ? k_mv<true> : k_mv<false>,
-                                                  kWarps * 32, smem);
-    if (per_sm <= 0) continue;
-    const uint64_t warps = (uint64_t)per_sm * kWarps, flight = warps * (d - 1) * sb;
-    if (warps > best_warps || (warps == best_warps && flight > best_flight)) {
-      best_d = d;
-      best_per_sm = per_sm;
-      best_warps = warps;
-      best_flight = flight;
+  {
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    auto it = g_plans.find(key);
+    if (it != g_plans.end()) {
+      best_d = it->second.first;
+      best_per_sm = it->second.second;
     }
   }
-  if (best_d == 0) {  // cannot happen when stream_applies() held; be safe
-    best_d = 2;
-    best_per_sm = 1;
+  if (best_d == 0) {
+    uint64_t best_warps = 0, best_flight = 0;
+    for (int d : {4, 3, 2}) {
+      const size_t smem = (size_t)kWarps * d * sb;
+      if (smem > dyn_max) continue;
+      int per_sm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kmv, kWarps * 32, smem);
+      if (per_sm <= 0) continue;
+      const uint64_t warps = (uint64_t)per_sm * kWarps, flight = warps * (d - 1) * sb;
+      if (warps > best_warps || (warps == best_warps && flight > best_flight)) {
+        best_d = d;
+        best_per_sm = per_sm;
+        best_warps = warps;
+        best_flight = flight;
+      }
+    }
+    if (best_d == 0) {  // cannot happen when stream_applies() held; be safe
+      best_d = 2;
+      best_per_sm = 1;
+    }
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    g_plans[key] = {best_d, best_per_sm};
   }
-  Args args{y.hdr, a.hdr, a.words, a.capacity, x.hdr, x.words, x.capacity, m, n,
-            yv,    ximg, 0u,     0u,         0u};
+  Args args{y.hdr, a.hdr, a.words, a.capacity, x.hdr, x.words, x.capacity, m, n, yv, ximg, 0u,
+            dp ? 1 : 0};
   args.ring_bytes = (uint32_t)best_d * sb;
-  args.x_offset = kWarps * args.ring_bytes;
-  args.x_bytes = xbytes;
-  const size_t smem = (size_t)args.x_offset + xbytes;
+  const size_t smem = (size_t)kWarps * args.ring_bytes;
   const uint64_t grid =
       umax(1, umin((uint64_t)num_sms() * best_per_sm, (T + kWarps - 1) / kWarps));
-  const unsigned gi =
-      (unsigned)umax(1, umin(umax(nchunks, (m + 1023) / 1024), (uint64_t)num_sms() * 4));
-  k_mv_init<<<gi, kInitThreads, 0, st>>>(args, ximg);
+  const unsigned gi = (unsigned)umax(1, umin(umax((nchunks + 7) / 8, (m + 2047) / 2048),
+                                             (uint64_t)num_sms() * 2));
+  k_mv_init<<<gi, kInitThreads, 0, st>>>(args);
   note_launch();
   const bool plain = profile_armed();  // timing the main kernel alone
-  auto kmv = narrow ? k_mv<true> : k_mv<false>;
   profile_begin(st);
   if (plain)
     kmv<<<(unsigned)grid, kWarps * 32, smem, st>>>(args);
@@ -211,11 +269,12 @@ void run_stream(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& y, v
   profile_end(st);
   note_launch();
   if (m <= kYSmallRows) {
+    const size_t ysmem = (size_t)((m + 31) / 32) * 33 * 8;
     if (plain)
-      k_mv_ypack<<<1, kYThreads, (size_t)m * 8, st>>>(y.hdr, y.words, y.capacity,
+      k_mv_ypack<<<1, kYThreads, ysmem, st>>>(y.hdr, y.words, y.capacity,
                                                        (const int64_t*)yv, m);
     else
-      ax::launch_pdl(k_mv_ypack, dim3(1), dim3(kYThreads), (size_t)m * 8, st, y.hdr, y.words,
+      ax::launch_pdl(k_mv_ypack, dim3(1), dim3(kYThreads), ysmem, st, y.hdr, y.words,
                      y.capacity, (const int64_t*)yv, m);
     note_launch();
   } else {
