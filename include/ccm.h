@@ -257,6 +257,25 @@ ccm_status ccm_gen_poisson(int64_t* out, uint64_t count, uint64_t seed, uint64_t
                            uint64_t start, const double* table, uint32_t table_len,
                            ccm_stream_t stream);
 
+/* Re-pack at a given width (Methods, Method 1: the same fields written with
+ * b = `width` bits each, two's complement when `is_signed`), into rows
+ * [row_offset, row_offset + in->rows) of `out` (out->rows >= that, same
+ * cols).  Every other word of out (its other rows, the bits above the block's
+ * last field, the pad words) is set to zero, and out's header describes the
+ * whole out->rows x cols matrix at `width`.  This is the assembly step of a
+ * matvec split by rows across devices: each device re-packs its block of y at
+ * the width all blocks agree on (the maximum of their width statistics), and
+ * since the blocks occupy disjoint word ranges, a sum (or OR) of the devices'
+ * word buffers is the packed y.  Host checks: width 1..64 (CCM_E_WIDTH),
+ * row_offset*cols*width a multiple of 32 for a non-empty block, i.e. the
+ * block starts on a word boundary (CCM_E_SHAPE; row_offset a multiple of 32
+ * always qualifies), out
+ * capacity for the whole matrix at `width` (CCM_E_CAPACITY).  On the GPU: an
+ * input whose width or sign mode does not fit the target gets CCM_E_WIDTH in
+ * out's header and no words are written.  out's stat_or/stat_neg are zero. */
+ccm_status ccm_repack(const ccm_matrix* in, int width, int is_signed, const ccm_matrix* out,
+                      uint64_t row_offset, ccm_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * Batched matvec: y_i = A_i x_i for many packed matrices of uneven shapes and
  * widths in one persistent launch (same arithmetic as ccm_matvec, applied to

@@ -97,6 +97,7 @@ SIGNATURES = {
     "ccm_bound_scale": ([_i32, _i32, _i64], _i32),
     "ccm_bound_matvec": ([_i32, _i32, _i32, _i32, _u64], _i32),
     "ccm_bound_matmul": ([_i32, _i32, _i32, _i32, _u64], _i32),
+    "ccm_repack": ([_MP, _i32, _i32, _MP, _u64, _vp], _i32),
     "ccm_launch_count": ([], _u64),
     "ccm_profile_next": ([_vp, _vp], _i32),
 }
@@ -355,6 +356,17 @@ def scale(a: PackedMatrix, s: int, capacity: int | None = None, stream=None):
     if capacity is None:
         capacity = words_for(a.rows, a.cols, bound_scale(a, s))
     return scale_into(a, s, PackedMatrix(a.rows, a.cols, capacity, a.device), stream)
+
+
+def repack_into(a: PackedMatrix, width: int, is_signed: int, out: PackedMatrix,
+                row_offset: int = 0, stream=None) -> PackedMatrix:
+    """a's fields at `width` (and sign mode) into rows [row_offset, +a.rows)
+    of out; every other word of out is zero (ccm_repack)."""
+    ma, mo = a.c(), out.c()
+    _check(lib().ccm_repack(ctypes.byref(ma), int(width), int(is_signed), ctypes.byref(mo),
+                            int(row_offset), _stream(stream)), "ccm_repack")
+    out._written()
+    return out
 
 
 def workspace_bytes(op: int, m: int, k: int, n: int) -> int:

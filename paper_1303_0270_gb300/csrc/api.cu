@@ -185,6 +185,19 @@ ccm_status ccm_matmul(const ccm_matrix* a, const ccm_matrix* b, const ccm_matrix
   return launched();
 }
 
+ccm_status ccm_repack(const ccm_matrix* in, int width, int is_signed, const ccm_matrix* out,
+                      uint64_t row_offset, ccm_stream_t stream) {
+  if (!valid_in(in) || !valid_out(out)) return CCM_E_INVAL;
+  if (width < 1 || width > 64 || (is_signed != 0 && is_signed != 1)) return CCM_E_WIDTH;
+  if (out->cols != in->cols || row_offset > out->rows || in->rows > out->rows - row_offset)
+    return CCM_E_SHAPE;
+  // a non-empty block must start on a word boundary of the output stream
+  if (in->rows && (row_offset * in->cols * (uint64_t)width) % 32) return CCM_E_SHAPE;
+  if (out->capacity < words_for(out->rows * out->cols, width)) return CCM_E_CAPACITY;
+  ccm::run_repack(*in, width, is_signed, *out, row_offset, to_cuda(stream));
+  return launched();
+}
+
 uint64_t ccm_vlb_index_entries(uint64_t rows, uint64_t cols) {
   return (rows * cols + CCM_VLB_INDEX_STRIDE - 1) / CCM_VLB_INDEX_STRIDE + 1;
 }

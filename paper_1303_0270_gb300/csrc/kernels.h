@@ -59,6 +59,9 @@ void run_matvec2(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& b,
 void run_matvec(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& y, void* ws,
                 cudaStream_t st);
 
+void run_repack(const ccm_matrix& in, int width, int is_signed, const ccm_matrix& out,
+                uint64_t row_offset, cudaStream_t st);
+
 size_t matmul_workspace(const ccm_matrix& a, const ccm_matrix& b);
 // Shape-only bound on matmul_workspace (the widths are unknown): the tensor
 // path at its widest (4 digits per field).

@@ -92,6 +92,15 @@ def test_host_side_rejections_launch_nothing(L):
                             bp(x), bp(y), ws, need - 1, None) == ccm.E_CAPACITY
     assert L.ccm_vlb_matvec(h, ctypes.c_void_p(0x7000), 8, ctypes.c_void_p(0x6000), 3, 4,
                             bp(x), bp(y), ctypes.c_void_p(0x10010), need, None) == ccm.E_INVAL
+    # repack: width range, shape, word alignment of the block, capacity
+    y, big = _m(40, 1, cap=64), _m(100, 1, cap=64)
+    assert L.ccm_repack(bp(y), 0, 0, bp(big), 0, None) == ccm.E_WIDTH
+    assert L.ccm_repack(bp(y), 65, 1, bp(big), 0, None) == ccm.E_WIDTH
+    assert L.ccm_repack(bp(y), 8, 2, bp(big), 0, None) == ccm.E_WIDTH
+    assert L.ccm_repack(bp(y), 8, 0, bp(big), 61, None) == ccm.E_SHAPE   # 61 + 40 > 100
+    assert L.ccm_repack(bp(y), 8, 0, bp(_m(100, 2, cap=64)), 0, None) == ccm.E_SHAPE
+    assert L.ccm_repack(bp(y), 9, 0, bp(big), 3, None) == ccm.E_SHAPE    # 27 bits in
+    assert L.ccm_repack(bp(y), 8, 0, bp(_m(100, 1, cap=24)), 0, None) == ccm.E_CAPACITY
     # generators
     assert L.ccm_gen_uniform(None, 5, 1, 0, 0, 0, 1, None) == ccm.E_INVAL
     assert L.ccm_gen_uniform(ctypes.c_void_p(0x4000), 5, 1, 0, 0, 3, 1, None) == ccm.E_INVAL
