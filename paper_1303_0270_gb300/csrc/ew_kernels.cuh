@@ -26,6 +26,7 @@
 
 #include <type_traits>
 
+#include "async_copy.cuh"
 #include "group_engine.cuh"
 #include "pack_engine.cuh"
 
@@ -722,6 +723,10 @@ __global__ void __launch_bounds__(kThreads) k_ew(Op op, ccm_header* out, uint32_
   using U = typename std::make_unsigned<V>::type;
   constexpr int kSignShift = 8 * sizeof(V) - 1;
   __shared__ __align__(16) uint32_t s_buf[kWarps][kBufWords];
+  // after a lane pass or a speculative pass this kernel is launched with
+  // programmatic dependent launch: wait for that kernel before reading the
+  // header it wrote (a no-op for a normal launch)
+  ax::grid_dep_wait();
   int b = 0, sgn = 0;
   if constexpr (MODE == kPack) {
     if (!resolve_output(out, words, capacity, n, b, sgn)) return;
@@ -1072,9 +1077,14 @@ int launch_ew_add(const EwCall& c, cudaStream_t st) {
   else if (c.kind == EwKind::AddSpec) {
     launch_lanes_add(op, c.out, c.words, c.capacity, n, C, st);
     launched = 2;
-    k_ew<OpAdd, C, kSpec><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity, n, 0);
-  } else
-    k_ew<OpAdd, C, kPack><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity, n, c.spec);
+    // the passes after the lane pass usually return at once: launched early
+    // (programmatic dependent launch) so that their launch overlaps it
+    ax::launch_pdl(k_ew<OpAdd, C, kSpec>, dim3(g), dim3(kThreads), 0, st, op, c.out, c.words,
+                   c.capacity, n, 0);
+  } else {
+    ax::launch_pdl(k_ew<OpAdd, C, kPack>, dim3(g), dim3(kThreads), 0, st, op, c.out, c.words,
+                   c.capacity, n, c.spec);
+  }
   return launched;
 }
 
@@ -1094,11 +1104,11 @@ int launch_ew_scale(const EwCall& c, cudaStream_t st) {
         launched = 2;
       }
     }
-    k_ew<OpScale<SMALL>, C, kSpec><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity, n,
-                                                           0);
+    ax::launch_pdl(k_ew<OpScale<SMALL>, C, kSpec>, dim3(g), dim3(kThreads), 0, st, op, c.out,
+                   c.words, c.capacity, n, 0);
   } else {
-    k_ew<OpScale<SMALL>, C, kPack><<<g, kThreads, 0, st>>>(op, c.out, c.words, c.capacity, n,
-                                                           c.spec);
+    ax::launch_pdl(k_ew<OpScale<SMALL>, C, kPack>, dim3(g), dim3(kThreads), 0, st, op, c.out,
+                   c.words, c.capacity, n, c.spec);
   }
   return launched;
 }

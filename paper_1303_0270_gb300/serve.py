@@ -71,42 +71,61 @@ class Server:
     """Continuous-batching loop over a resident store of packed matrices."""
 
     def __init__(self, store, mem_budget: int, streams: int = 4, batching: bool = True,
-                 device=None):
+                 device=None, heavy_streams: int = 2):
         self.store = store                     # list of PackedMatrix (resident)
         self.device = device or store[0].device
         self.mem_budget = int(mem_budget)
-        self.streams = [torch.cuda.Stream(self.device) for _ in range(streams)]
-        self.busy = [None] * streams           # what runs on each stream
+        # matvecs and packs (sub-millisecond) on high-priority streams, matmuls
+        # (up to ~10^2 ms at 8192^3) on low-priority ones: when SMs free up,
+        # the short requests' blocks are scheduled first
+        lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream,
+                                                                "priority_range") else (0, 0)
+        self.light = list(range(streams))
+        self.heavy = list(range(streams, streams + heavy_streams)) if heavy_streams else []
+        self.streams = ([torch.cuda.Stream(self.device, priority=hi) for _ in self.light] +
+                        [torch.cuda.Stream(self.device, priority=lo) for _ in self.heavy])
+        self.busy = [None] * len(self.streams)  # what runs on each stream
         self.batching = batching
         self.used = sum(4 * (ccm.HEADER_WORDS + m.capacity) for m in store)
 
     # -- per-request resources ---------------------------------------------
-    def _out_bytes(self, r: Request) -> int:
+    def _out_capacity(self, r: Request) -> int:
+        """Output words: the library's result-width bound (matvec, matmul);
+        64 bits per entry for a pack, whose width is only known once packed."""
         if r.kind == "matvec":
             a = self.store[r.a]
-            return 4 * ccm.words_for(a.rows, 1, 64) + 64 + 16 * a.rows + 8 * a.cols + 512
+            return ccm.words_for(a.rows, 1, ccm.bound_matvec(a, r.x))
         if r.kind == "pack":
             rows, cols = r.dense.shape
-            return 4 * ccm.words_for(rows, cols, 64) + ccm.workspace_bytes(
-                ccm.OP_PACK, rows, cols, ccm.words_for(rows, cols, 64)) + 64
+            return ccm.words_for(rows, cols, 64)
         a, b = self.store[r.a], self.store[r.b]
-        return 4 * ccm.words_for(a.rows, b.cols, 64) + ccm.workspace_bytes(
-            ccm.OP_MATMUL, a.rows, a.cols, b.cols) + 64
+        return ccm.words_for(a.rows, b.cols, ccm.bound_matmul(a, b))
+
+    def _out_bytes(self, r: Request) -> int:
+        cap = 4 * self._out_capacity(r) + 64
+        if r.kind == "matvec":
+            a = self.store[r.a]
+            return cap + 16 * a.rows + 8 * a.cols + 512
+        if r.kind == "pack":
+            rows, cols = r.dense.shape
+            return cap + ccm.workspace_bytes(ccm.OP_PACK, rows, cols, self._out_capacity(r))
+        a, b = self.store[r.a], self.store[r.b]
+        return cap + ccm.workspace_bytes(ccm.OP_MATMUL, a.rows, a.cols, b.cols)
 
     def _launch_single(self, r: Request, s: torch.cuda.Stream):
         with torch.cuda.stream(s):
+            cap = self._out_capacity(r)
             if r.kind == "pack":
                 rows, cols = r.dense.shape
-                r.out = ccm.PackedMatrix(rows, cols, ccm.words_for(rows, cols, 64), self.device)
+                r.out = ccm.PackedMatrix(rows, cols, cap, self.device)
                 ccm.pack_into(r.dense, r.out, stream=s)
             elif r.kind == "matmul":
                 a, b = self.store[r.a], self.store[r.b]
-                r.out = ccm.PackedMatrix(a.rows, b.cols, ccm.words_for(a.rows, b.cols, 64),
-                                         self.device)
+                r.out = ccm.PackedMatrix(a.rows, b.cols, cap, self.device)
                 ccm.matmul_into(a, b, r.out, stream=s)
             else:
                 a = self.store[r.a]
-                r.out = ccm.PackedMatrix(a.rows, 1, ccm.words_for(a.rows, 1, 64), self.device)
+                r.out = ccm.PackedMatrix(a.rows, 1, cap, self.device)
                 ccm.matvec_into(a, r.x, r.out, stream=s)
             r.event = torch.cuda.Event()
             r.event.record(s)
@@ -114,7 +133,8 @@ class Server:
     def _launch_batch(self, reqs, s: torch.cuda.Stream):
         mats = [self.store[r.a] for r in reqs]
         xs = [r.x for r in reqs]
-        ys = [ccm.PackedMatrix(m.rows, 1, ccm.words_for(m.rows, 1, 64), self.device) for m in mats]
+        ys = [ccm.PackedMatrix(self.store[r_.a].rows, 1, self._out_capacity(r_), self.device)
+              for r_ in reqs]
         with torch.cuda.stream(s):
             bm = BatchMatvec(mats, xs, ys, unit_segments=256)
             bm.launch(stream=s)
@@ -126,7 +146,11 @@ class Server:
         return bm
 
     # -- the loop ----------------------------------------------------------
-    def run(self, trace, stats: Stats | None = None, max_batch: int = 512) -> Stats:
+    def run(self, trace, stats: Stats | None = None, max_batch: int = 512,
+            keep_result=None) -> Stats:
+        """Serve the trace.  `keep_result(r)` says whether request r's result
+        stays attached to it after completion (default: all); the others are
+        dropped as they complete, as a server hands results back."""
         stats = stats or Stats()
         pending = deque(sorted(trace, key=lambda r: r.arrival))
         waiting: deque = deque()
@@ -146,15 +170,32 @@ class Server:
                         stats.latencies.append(r.done - r.arrival)
                         stats.kinds.append(r.kind)
                         self.used -= r.nbytes
+                        if keep_result is not None and not keep_result(r):
+                            r.out = None
+                        r.event = None
                     self.busy[slot] = None
                 else:
                     still.append((slot, reqs, keep))
             inflight = still
-            # admit in arrival order while a slot is free and memory fits
-            free = [i for i, b in enumerate(self.busy) if b is None]
+            # admit in arrival order while a slot of the request's class is free
+            # and memory fits
+            free = [i for i in self.light if self.busy[i] is None]
+            free_heavy = [i for i in self.heavy if self.busy[i] is None]
             launched = False
-            while free and waiting:
-                head = waiting[0]
+            while waiting:
+                # the first waiting request whose class has a free slot (a
+                # matmul waiting for a heavy slot does not hold up the rest)
+                head, pool = None, None
+                for r in waiting:
+                    heavy = r.kind == "matmul" and bool(self.heavy)
+                    if heavy and free_heavy:
+                        head, pool = r, free_heavy
+                        break
+                    if not heavy and free:
+                        head, pool = r, free
+                        break
+                if head is None:
+                    break
                 if self.batching and head.kind == "matvec":
                     group, need = [], 0
                     for r in list(waiting):
@@ -172,7 +213,7 @@ class Server:
                         r.nbytes = self._out_bytes(r)
                         r.admitted = now
                     self.used += need
-                    slot = free.pop(0)
+                    slot = pool.pop(0)
                     keep = self._launch_batch(group, self.streams[slot])
                     self.busy[slot] = group
                     inflight.append((slot, group, keep))
@@ -182,11 +223,11 @@ class Server:
                     nb = self._out_bytes(head)
                     if self.used + nb > self.mem_budget:
                         break
-                    waiting.popleft()
+                    waiting.remove(head)
                     head.nbytes = nb
                     head.admitted = now
                     self.used += nb
-                    slot = free.pop(0)
+                    slot = pool.pop(0)
                     self._launch_single(head, self.streams[slot])
                     self.busy[slot] = [head]
                     inflight.append((slot, [head], None))
@@ -210,10 +251,11 @@ def run_alone(store, r: Request, device) -> "ccm.PackedMatrix":
         return ccm.pack_into(r.dense, out)
     if r.kind == "matmul":
         a, b = store[r.a], store[r.b]
-        out = ccm.PackedMatrix(a.rows, b.cols, ccm.words_for(a.rows, b.cols, 64), device)
+        out = ccm.PackedMatrix(a.rows, b.cols, ccm.words_for(a.rows, b.cols,
+                                                             ccm.bound_matmul(a, b)), device)
         return ccm.matmul_into(a, b, out)
     a = store[r.a]
-    out = ccm.PackedMatrix(a.rows, 1, ccm.words_for(a.rows, 1, 64), device)
+    out = ccm.PackedMatrix(a.rows, 1, ccm.words_for(a.rows, 1, ccm.bound_matvec(a, r.x)), device)
     return ccm.matvec_into(a, r.x, out)
 
 
