@@ -347,7 +347,7 @@ def run_gpu(args, rank, world, local_rank):
     kernels = {"pack": "ge::k_pack_local<int64_t, 8>", "unpack": "ge::k_unpack_ge<int64_t, 8>",
                "add": "ge::k_ew_lanes<OpAdd> (+ k_ew spec/finish, which return at once)",
                "scale": "ge::k_ew_lanes<OpScale<true>> (+ k_ew spec/finish, which return at once)",
-               "matvec": "mvf::k_matvec_rows<8, narrow>"}
+               "matvec": "mvs::k_mv<byte lanes, narrow>"}
     per_op = {}
     for k, t in kern_ms.items():
         gbs = ops[k] / (t * 1e-3) / 1e9
@@ -474,7 +474,7 @@ def batch_measure(torch, ccm, dev, count, seed, steps, warmup):
     return {"workload": f"{count} packed matrices, rows/cols log-uniform [16, 2048), "
                         "widths U{1..24}, signed uniform values, x signed 8-bit",
             "packed_bytes": packed_bytes, "fields": int((rows * cols).sum()),
-            "autotune": {k: tune[k] for k in ("unit_segments", "grid") if k in tune},
+            "autotune": {k: tune[k] for k in ("unit_segments", "grid", "slots") if k in tune},
             "ms": round(ms_batch, 4), "GB/s": round(gbs, 2), "frac_of_hbm": round(gbs / hbm, 4),
             "plain_ms": round(ms_plain, 3), "speedup_vs_plain": round(ms_plain / ms_batch, 2),
             "mismatches_vs_plain": bad, "timing": f"mean of {steps} graph replays, CUDA events"}

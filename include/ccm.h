@@ -296,9 +296,10 @@ ccm_status ccm_repack(const ccm_matrix* in, int width, int is_signed, const ccm_
  * clears y headers and the scratch) and the persistent kernel (`grid` CTAs;
  * <= 0 picks 3 per SM).  The initialisation kernel (one block per entry)
  * also decodes every x into an int32 image in `ws`; the main kernel's shared
- * memory holds each warp's two staging slots for A widths up to
+ * memory holds each warp's info->slots staging slots for A widths up to
  * info->max_width (an info with max_width outside 1..32 or max_cols above
- * 8192: CCM_E_INVAL).  `ws` is device workspace of at least
+ * 8192, or slots other than 0, 2 or 4, or slots whose shared memory exceeds the
+ * device's: CCM_E_INVAL).  `ws` is device workspace of at least
  * ccm_batch_workspace_bytes(...) bytes, 256-byte aligned.  Each y_i header
  * receives its own status.  Both launches are stream-ordered and can be
  * captured in a CUDA graph. */
@@ -316,7 +317,8 @@ typedef struct ccm_batch_info {
   uint32_t max_cols;      /* widest entry (at most 8192 columns) */
   uint64_t plan_bytes;
   uint32_t max_width;     /* widest A the capacities admit, <= 32 (sizes the staging) */
-  uint32_t reserved;
+  uint32_t slots;         /* ring slots per warp, 2 or 4 (set by the plan to 2; the caller
+                             may set 4 before ccm_batch_matvec: three chunks in flight) */
   uint64_t x_ints;        /* ints of the decoded-x images in the workspace */
 } ccm_batch_info;
 

@@ -35,6 +35,7 @@ class BatchMatvec:
             self.entries[i].a, self.entries[i].x, self.entries[i].y = a.c(), x.c(), y.c()
         self.count = n
         self.grid = grid
+        self.slots = 2  # ring slots per warp (2 or 4)
         self.graph = None
         L = ccm.lib()
         ws = L.ccm_batch_workspace_bytes(self.entries, n)
@@ -57,6 +58,7 @@ class BatchMatvec:
 
     def launch(self, stream=None):
         """Both launches of one batched matvec, asynchronous."""
+        self.info.slots = self.slots
         ccm._check(ccm.lib().ccm_batch_matvec(
             ctypes.c_void_p(self.plan.data_ptr()), ctypes.byref(self.info),
             ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(), int(self.grid),
@@ -94,8 +96,8 @@ class BatchMatvec:
         return h.hexdigest()[:24]
 
     def autotune(self, candidates=None, reps: int = 3, cache: str | None = None):
-        """Time each (unit_segments, grid) candidate on this batch and keep the
-        fastest; results are cached by batch signature (in memory and, when
+        """Time each (unit_segments, grid, ring slots) candidate on this batch
+        and keep the fastest; results are cached by batch signature (in memory and, when
         `cache` or $CCM_AUTOTUNE_CACHE names a file, on disk)."""
         cache = cache or os.environ.get("CCM_AUTOTUNE_CACHE")
         key = self.signature()
@@ -106,17 +108,29 @@ class BatchMatvec:
         if key in store:
             us, grid = store[key]["unit_segments"], store[key]["grid"]
             self.grid = grid
+            self.slots = store[key].get("slots", 2)
             if us != self.unit_segments:
                 self.set_unit_segments(us)
             return store[key]
         sms = torch.cuda.get_device_properties(self.device).multi_processor_count
         if candidates is None:
-            candidates = [(us, g * sms) for us in (128, 256, 512, 1024) for g in (2, 4, 6)]
+            # work-unit size x persistent grid x ring depth (chunks of 32
+            # segments, one segment of 32 fields per lane, in flight per warp)
+            candidates = [(us, g * sms, k) for us in (512, 1024, 2048, 4096)
+                          for g in (1, 2, 3, 4) for k in (2, 4)]
         best = None
         results = []
-        for us, grid in candidates:
-            self.set_unit_segments(us)
+        for cand in candidates:
+            us, grid = cand[0], cand[1]
+            slots = cand[2] if len(cand) > 2 else 2
+            if us != self.unit_segments or self.plan is None:
+                self.set_unit_segments(us)
             self.grid = grid
+            self.slots = slots
+            try:
+                self.launch()
+            except ccm.CCMError:
+                continue  # (ring too large for shared memory at this width bound)
             self.launch()
             torch.cuda.synchronize(self.device)
             times = []
@@ -129,11 +143,12 @@ class BatchMatvec:
                 e1.synchronize()
                 times.append(e0.elapsed_time(e1))
             t = min(times)
-            results.append({"unit_segments": us, "grid": grid, "ms": t})
+            results.append({"unit_segments": us, "grid": grid, "slots": slots, "ms": t})
             if best is None or t < best["ms"]:
-                best = {"unit_segments": us, "grid": grid, "ms": t}
+                best = {"unit_segments": us, "grid": grid, "slots": slots, "ms": t}
         self.set_unit_segments(best["unit_segments"])
         self.grid = best["grid"]
+        self.slots = best["slots"]
         best["tried"] = results
         store[key] = best
         if cache:

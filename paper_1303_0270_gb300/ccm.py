@@ -54,7 +54,7 @@ class BatchInfo(ctypes.Structure):
     _fields_ = [("count", ctypes.c_uint32), ("units", ctypes.c_uint32),
                 ("y_rows", ctypes.c_uint64), ("unit_segments", ctypes.c_uint32),
                 ("max_cols", ctypes.c_uint32), ("plan_bytes", ctypes.c_uint64),
-                ("max_width", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("max_width", ctypes.c_uint32), ("slots", ctypes.c_uint32),
                 ("x_ints", ctypes.c_uint64)]
 
 

@@ -4,9 +4,9 @@
 // Work unit: a run of consecutive 32-field row segments of one matrix.  Row i
 // of an m x n matrix is cut into ceil(n / 32) segments of up to 32 fields; a
 // lane owns one segment.  A warp takes 32 consecutive segments at a time (a
-// chunk: one contiguous word range) and streams its chunks through a
-// two-slot cp.async ring in shared memory, so the words of the next chunk are
-// in flight while the current one is decoded.  A segment starts at an
+// chunk: one contiguous word range) and streams its chunks through a ring of
+// K = 2 or 4 cp.async slots in shared memory, so the words of the next K - 1
+// chunks are in flight while the current one is decoded.  A segment starts at an
 // arbitrary bit, so the lane reads the b + 1 words that cover it,
 // funnel-shifts them once to the segment's start and then decodes its fields
 // with shifts fixed at compile time (the width is dispatched per unit on the
@@ -98,6 +98,7 @@ struct Args {
   int* ximage;          // decoded x of every matrix (Mat::x_off)
   uint32_t slot;        // shared words of one ring slot (slot_words(bmax))
   uint32_t bmax;        // widest A the slots hold
+  uint32_t slots;       // ring slots per warp: 2 or 4
 };
 
 __device__ __forceinline__ int stage_pos(int w, int b) { return (b & 1) ? w : w + (w >> 5); }
@@ -190,34 +191,31 @@ __global__ void k_batch_init(Args a) {
 // ---------------------------------------------------------------------------
 // One unit at compile-time width B.
 // ---------------------------------------------------------------------------
-template <int B, bool SGN>
+template <int B, bool SGN, int K>
 __device__ __noinline__ void run_unit(const Mat& M, const Unit& u, const int4* __restrict__ x4,
                                       uint32_t* stage, uint32_t slot_w, int64_t* ys) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const uint32_t n = M.n, nsr = M.nseg_row;
   const uint64_t dw = data_words((uint64_t)M.m * n, B);
-  uint32_t* slots[2] = {stage, stage + slot_w};
+  constexpr uint32_t kStep = kWarps * 32;  // segments between a warp's chunks
   uint32_t base = warp * 32;
-  uint64_t w_first = 0;  // of chunk k (the one decoded next)
-  if (base < u.nseg) {
-    const Chunk c = chunk_of<B>(M, u, base);
-    w_first = c.w_first;
-    issue_chunk<B>(M.wa, dw, c, slots[0], lane);
-  }
-  cp_async_commit();
-  for (uint32_t k = 0; base < u.nseg; base += kWarps * 32, ++k) {
-    // the next chunk's words in flight while this one is decoded
-    const uint32_t nb = base + kWarps * 32;
-    uint64_t w_next = 0;
-    if (nb < u.nseg) {
-      const Chunk c = chunk_of<B>(M, u, nb);
-      w_next = c.w_first;
-      issue_chunk<B>(M.wa, dw, c, slots[(k + 1) & 1], lane);
-    }
+  // the first K - 1 chunks in flight (one commit group each, empty or not)
+#pragma unroll
+  for (int p = 0; p < K - 1; ++p) {
+    const uint32_t bp = base + p * kStep;
+    if (bp < u.nseg) issue_chunk<B>(M.wa, dw, chunk_of<B>(M, u, bp), stage + p * slot_w, lane);
     cp_async_commit();
-    cp_async_wait<1>();  // chunk k has landed (groups complete in order)
+  }
+  for (uint32_t k = 0; base < u.nseg; base += kStep, ++k) {
+    // K - 1 chunks in flight while this one is decoded
+    const uint32_t nb = base + (K - 1) * kStep;
+    if (nb < u.nseg)
+      issue_chunk<B>(M.wa, dw, chunk_of<B>(M, u, nb), stage + ((k + K - 1) % K) * slot_w, lane);
+    cp_async_commit();
+    cp_async_wait<K - 1>();  // chunk k has landed (groups complete in order)
     __syncwarp();
-    const uint32_t* sg = slots[k & 1];
+    const uint64_t w_first = chunk_of<B>(M, u, base).w_first;
+    const uint32_t* sg = stage + (k % K) * slot_w;
     // the warp's 32 consecutive segments; lane -> (row, segment in the row)
     const uint32_t id = u.seg0 + base + lane;
     const bool live = base + lane < u.nseg;
@@ -261,8 +259,7 @@ __device__ __noinline__ void run_unit(const Mat& M, const Unit& u, const int4* _
         }
       }
     }
-    __syncwarp();  // slot k & 1 is refilled by the issue of chunk k + 2
-    w_first = w_next;
+    __syncwarp();  // slot k % K is refilled by the issue of chunk k + K
     // segmented reduction by row: the first lane of each row gets the total
     uint32_t r = row;
 #pragma unroll
@@ -351,12 +348,14 @@ __global__ void __launch_bounds__(kThreads) k_batch_mv(Args a) {
     if (ok) {
       const int b = M.ha->width, sgn = M.ha->is_signed;
       int64_t* ys = a.yscratch + M.y_off;
-      uint32_t* stage = s_slots + (threadIdx.x / 32) * 2 * a.slot;
+      uint32_t* stage = s_slots + (threadIdx.x / 32) * a.slots * a.slot;
       const int4* x4 = reinterpret_cast<const int4*>(a.ximage + M.x_off);
-      switch (2 * b + sgn) {
-#define CCM_BT_CASE(B)                                                              \
-  case 2 * B: run_unit<B, false>(M, u, x4, stage, a.slot, ys); break; \
-  case 2 * B + 1: run_unit<B, true>(M, u, x4, stage, a.slot, ys); break;
+      switch (4 * b + 2 * sgn + (a.slots == 4 ? 1 : 0)) {
+#define CCM_BT_CASE(B)                                                                    \
+  case 4 * B: run_unit<B, false, 2>(M, u, x4, stage, a.slot, ys); break;      \
+  case 4 * B + 1: run_unit<B, false, 4>(M, u, x4, stage, a.slot, ys); break;  \
+  case 4 * B + 2: run_unit<B, true, 2>(M, u, x4, stage, a.slot, ys); break;   \
+  case 4 * B + 3: run_unit<B, true, 4>(M, u, x4, stage, a.slot, ys); break;
         CCM_BT_CASE(1) CCM_BT_CASE(2) CCM_BT_CASE(3) CCM_BT_CASE(4) CCM_BT_CASE(5)
         CCM_BT_CASE(6) CCM_BT_CASE(7) CCM_BT_CASE(8) CCM_BT_CASE(9) CCM_BT_CASE(10)
         CCM_BT_CASE(11) CCM_BT_CASE(12) CCM_BT_CASE(13) CCM_BT_CASE(14) CCM_BT_CASE(15)
@@ -520,7 +519,7 @@ ccm_status ccm_batch_plan(const ccm_batch_entry* entries, int count, uint32_t un
   info->count = (uint32_t)count;
   info->max_cols = (uint32_t)maxcols;
   info->max_width = (uint32_t)maxw;
-  info->reserved = 0;
+  info->slots = 2;
   info->x_ints = xoff;
   info->units = L.nunits;
   info->y_rows = L.yrows;
@@ -556,7 +555,10 @@ ccm_status ccm_batch_matvec(const void* plan, const ccm_batch_info* info, void* 
     return CCM_E_INVAL;
   a.slot = slot_words((int)info->max_width);
   a.bmax = info->max_width;
-  const size_t smem = (size_t)kWarps * 2 * a.slot * sizeof(uint32_t);
+  if (info->slots != 0 && info->slots != 2 && info->slots != 4) return CCM_E_INVAL;
+  a.slots = info->slots == 4 ? 4 : 2;
+  const size_t smem = (size_t)kWarps * a.slots * a.slot * sizeof(uint32_t);
+  if (smem > (size_t)ccm::max_smem_optin()) return CCM_E_INVAL;
   if (grid <= 0) grid = ccm::num_sms() * 3;
   static size_t attr = 0;
   if (smem > attr) {

@@ -88,12 +88,110 @@ __device__ __forceinline__ int digit(int64_t a, int l, int L) {
   return l == L - 1 ? (int)(a >> (4 * l)) : (int)((a >> (4 * l)) & 15);
 }
 
+// ---------------------------------------------------------------------------
+// Fields of exactly 4L bits: digit l of field f is nibble f L + l of the
+// packed stream (the stream is LSB-first and the digits are the value's
+// nibbles, the top one taken as signed for two's complement fields), so the
+// digit planes are a strided nibble gather.  Four nibbles become four e4m3
+// bytes by table lookup with byte permutes: the low three bits of a nibble
+// select a byte of an 8-byte table (entries 0..7, or 8..15 / the negative
+// digits -8..-1), bit 3 picks which table.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t e4m3_of_nibbles(uint32_t x, bool top_signed) {
+  // e4m3 of 0..7, 8..15, and of -8..-1 (nibbles 8..15 of a signed digit)
+  constexpr uint32_t kLo0 = 0x44403800u, kLo1 = 0x4E4C4A48u;
+  constexpr uint32_t kHi0 = 0x53525150u, kHi1 = 0x57565554u;
+  constexpr uint32_t kNeg0 = 0xCACCCED0u, kNeg1 = 0xB8C0C4C8u;
+  const uint32_t sel = x & 0x7777u;
+  const uint32_t lo = __byte_perm(kLo0, kLo1, sel);
+  const uint32_t hi = top_signed ? __byte_perm(kNeg0, kNeg1, sel) : __byte_perm(kHi0, kHi1, sel);
+  const uint32_t big = __byte_perm(0u, 0xFFFFFFFFu, (x >> 1) & 0x4444u);  // 0xFF where bit 3
+  return (lo & ~big) | (hi & big);
+}
+
+// The 8 digit bytes of plane l for 8 consecutive fields held in w[0..L)
+// (32 L bits: 8 fields of 4L bits), as two words (fields 0..3, 4..7).
+template <int L>
+__device__ __forceinline__ uint2 plane_bytes8(const uint32_t (&w)[L], int l, bool top_signed) {
+  uint32_t x0 = 0, x1 = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int j = q * L + l;  // nibble index in the 8-field group
+    const uint32_t nib = (w[j >> 3] >> (4 * (j & 7))) & 15u;
+    if (q < 4)
+      x0 |= nib << (4 * q);
+    else
+      x1 |= nib << (4 * (q - 4));
+  }
+  return make_uint2(e4m3_of_nibbles(x0, top_signed), e4m3_of_nibbles(x1, top_signed));
+}
+
+// The L words holding fields [f0, f0 + 8) of a stream of 4L-bit fields (f0 a
+// multiple of 8, so the group starts on a word).
+template <int L>
+__device__ __forceinline__ void load_group8(const uint32_t* __restrict__ w, uint64_t f0,
+                                            uint32_t (&out)[L]) {
+  const uint32_t* p = w + f0 * L / 8;
+  if constexpr (L == 1) {
+    out[0] = __ldg(p);
+  } else if constexpr (L == 2) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+    out[0] = v.x;
+    out[1] = v.y;
+  } else if constexpr (L == 4) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+    out[0] = v.x;
+    out[1] = v.y;
+    out[2] = v.z;
+    out[3] = v.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < L; ++i) out[i] = __ldg(p + i);
+  }
+}
+
+// A (m x k, row-major, k % 8 == 0) with fields of exactly 4L bits ->
+// planes [L][m_pad][k_pad]: thread per 8 consecutive fields of a row.
+template <int L>
+__device__ void limbs_a_nibbles(const uint32_t* __restrict__ w, int sgn, uint64_t m, uint64_t k,
+                                uint64_t m_pad, uint64_t k_pad, uint8_t* __restrict__ planes) {
+  const uint64_t plane = m_pad * k_pad;
+  const uint32_t groups = (uint32_t)(k_pad / 8);
+  for (uint64_t i = blockIdx.x; i < m_pad; i += gridDim.x) {
+    for (uint32_t q = threadIdx.x; q < groups; q += blockDim.x) {
+      const uint64_t kk = 8ull * q;
+      uint2 out[L];
+      if (i < m && kk < k) {
+        uint32_t wg[L];
+        load_group8<L>(w, i * k + kk, wg);
+#pragma unroll
+        for (int l = 0; l < L; ++l) out[l] = plane_bytes8<L>(wg, l, sgn && l == L - 1);
+      } else {
+#pragma unroll
+        for (int l = 0; l < L; ++l) out[l] = make_uint2(0u, 0u);
+      }
+#pragma unroll
+      for (int l = 0; l < L; ++l)
+        *reinterpret_cast<uint2*>(planes + l * plane + i * k_pad + kk) = out[l];
+    }
+  }
+}
+
 // A (m x k, row-major) -> planes [L][m_pad][k_pad] of e4m3 digits.
 __global__ void k_limbs_a(const ccm_header* out, const ccm_header* h, const uint32_t* __restrict__ w,
                           uint64_t m, uint64_t k, uint64_t m_pad, uint64_t k_pad, int L,
                           uint8_t* __restrict__ planes) {
   if (out->status != CCM_OK) return;
   const int b = h->width, sgn = h->is_signed;
+  if (b == 4 * L && k % 8 == 0) {  // nibble-aligned fields
+    switch (L) {
+      case 1: limbs_a_nibbles<1>(w, sgn, m, k, m_pad, k_pad, planes); return;
+      case 2: limbs_a_nibbles<2>(w, sgn, m, k, m_pad, k_pad, planes); return;
+      case 3: limbs_a_nibbles<3>(w, sgn, m, k, m_pad, k_pad, planes); return;
+      case 4: limbs_a_nibbles<4>(w, sgn, m, k, m_pad, k_pad, planes); return;
+      default: break;
+    }
+  }
   const uint64_t quads = m_pad * k_pad / 4;
   const uint64_t plane = m_pad * k_pad;
   for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < quads;
@@ -122,15 +220,45 @@ __global__ void __launch_bounds__(256) k_limbs_bt(const ccm_header* out, const c
   const int b = h->width, sgn = h->is_signed;
   const uint64_t plane = n_pad * k_pad;
   const uint64_t tiles_k = k_pad / 64, tiles_n = n_pad / 32;
+  // nibble-aligned fields (b = 4L <= 16) and rows of whole 8-field groups:
+  // thread t reads fields j = 8 (t % 4) .. + 7 of row kk = t / 4 of the tile
+  const bool nib = b == 4 * L && L <= 4 && n % 8 == 0;
   for (uint64_t t = blockIdx.x; t < tiles_k * tiles_n; t += gridDim.x) {
     const uint64_t k0 = (t % tiles_k) * 64, j0 = (t / tiles_k) * 32;
     for (int l0 = 0; l0 < L; l0 += 4) {
-      // read: thread covers (kk = threadIdx.x / 32 + 8 r, j = threadIdx.x % 32)
-      for (int r = 0; r < 8; ++r) {
-        const int kk = threadIdx.x / 32 + 8 * r, j = threadIdx.x % 32;
-        const uint64_t gk = k0 + kk, gj = j0 + j;
-        const int64_t v = (gk < k && gj < n) ? decode_field(w, gk * n + gj, b, sgn) : 0;
-        for (int l = l0; l < L && l < l0 + 4; ++l) tile[l - l0][j][kk] = e4m3_of_digit(digit(v, l, L));
+      if (nib) {
+        const int kk = threadIdx.x / 4, jg = 8 * (threadIdx.x % 4);
+        const uint64_t gk = k0 + kk, gj = j0 + jg;
+        uint2 bytes[4] = {};
+        const bool live = gk < k && gj < n;
+        switch (L) {
+#define CCM_TC_NIB(LL)                                                           \
+  case LL:                                                                       \
+    if (live) {                                                                  \
+      uint32_t wg[LL];                                                           \
+      load_group8<LL>(w, gk * n + gj, wg);                                       \
+      _Pragma("unroll") for (int l = 0; l < LL; ++l) bytes[l] =                  \
+          plane_bytes8<LL>(wg, l, sgn && l == LL - 1);                           \
+    }                                                                            \
+    break;
+          CCM_TC_NIB(1) CCM_TC_NIB(2) CCM_TC_NIB(3) CCM_TC_NIB(4)
+#undef CCM_TC_NIB
+          default: break;
+        }
+        for (int l = 0; l < L; ++l) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            tile[l][jg + q][kk] = (uint8_t)((q < 4 ? bytes[l].x : bytes[l].y) >> (8 * (q & 3)));
+        }
+      } else {
+        // read: thread covers (kk = threadIdx.x / 32 + 8 r, j = threadIdx.x % 32)
+        for (int r = 0; r < 8; ++r) {
+          const int kk = threadIdx.x / 32 + 8 * r, j = threadIdx.x % 32;
+          const uint64_t gk = k0 + kk, gj = j0 + j;
+          const int64_t v = (gk < k && gj < n) ? decode_field(w, gk * n + gj, b, sgn) : 0;
+          for (int l = l0; l < L && l < l0 + 4; ++l)
+            tile[l - l0][j][kk] = e4m3_of_digit(digit(v, l, L));
+        }
       }
       __syncthreads();
       // write: 32 rows (j) x 64 bytes per digit plane, 16 bytes per thread

@@ -153,16 +153,20 @@ class Server:
         dropped as they complete, as a server hands results back."""
         stats = stats or Stats()
         pending = deque(sorted(trace, key=lambda r: r.arrival))
-        waiting: deque = deque()
+        # one FIFO per kind: admission looks at the three heads only
+        queues = {"matvec": deque(), "pack": deque(), "matmul": deque()}
+        nwait = 0
         inflight = []          # (slot, [requests], keepalive)
         t0 = time.perf_counter()
-        while pending or waiting or inflight:
+        while pending or nwait or inflight:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
-                waiting.append(pending.popleft())
+                r = pending.popleft()
+                queues[r.kind].append(r)
+                nwait += 1
             # retire finished work and free its slot and memory
             still = []
-            for slot, reqs, keep in inflight:
+            for slot, reqs, keepalive in inflight:
                 if reqs[0].event.query():
                     tdone = time.perf_counter() - t0
                     for r in reqs:
@@ -175,55 +179,53 @@ class Server:
                         r.event = None
                     self.busy[slot] = None
                 else:
-                    still.append((slot, reqs, keep))
+                    still.append((slot, reqs, keepalive))
             inflight = still
-            # admit in arrival order while a slot of the request's class is free
-            # and memory fits
+            # admit, earliest arrival first among the kinds whose slot class
+            # has a free slot (a matmul waiting for a heavy slot does not hold
+            # up the rest), while memory fits
             free = [i for i in self.light if self.busy[i] is None]
             free_heavy = [i for i in self.heavy if self.busy[i] is None]
             launched = False
-            while waiting:
-                # the first waiting request whose class has a free slot (a
-                # matmul waiting for a heavy slot does not hold up the rest)
+            while nwait:
                 head, pool = None, None
-                for r in waiting:
-                    heavy = r.kind == "matmul" and bool(self.heavy)
-                    if heavy and free_heavy:
-                        head, pool = r, free_heavy
-                        break
-                    if not heavy and free:
-                        head, pool = r, free
-                        break
+                for kind, q in queues.items():
+                    if not q:
+                        continue
+                    heavy = kind == "matmul" and bool(self.heavy)
+                    p = free_heavy if heavy else free
+                    if p and (head is None or q[0].arrival < head.arrival):
+                        head, pool = q[0], p
                 if head is None:
                     break
+                q = queues[head.kind]
                 if self.batching and head.kind == "matvec":
                     group, need = [], 0
-                    for r in list(waiting):
-                        if r.kind != "matvec" or len(group) >= max_batch:
-                            continue
-                        nb = self._out_bytes(r)
+                    while q and len(group) < max_batch:
+                        nb = self._out_bytes(q[0])
                         if self.used + need + nb > self.mem_budget:
                             break
+                        r = q.popleft()
+                        r.nbytes = nb
+                        r.admitted = now
                         group.append(r)
                         need += nb
                     if not group:
                         break
-                    for r in group:
-                        waiting.remove(r)
-                        r.nbytes = self._out_bytes(r)
-                        r.admitted = now
+                    nwait -= len(group)
                     self.used += need
                     slot = pool.pop(0)
-                    keep = self._launch_batch(group, self.streams[slot])
+                    keepalive = self._launch_batch(group, self.streams[slot])
                     self.busy[slot] = group
-                    inflight.append((slot, group, keep))
+                    inflight.append((slot, group, keepalive))
                     stats.batches += 1
                     stats.batched_matvecs += len(group)
                 else:
                     nb = self._out_bytes(head)
                     if self.used + nb > self.mem_budget:
                         break
-                    waiting.remove(head)
+                    q.popleft()
+                    nwait -= 1
                     head.nbytes = nb
                     head.admitted = now
                     self.used += nb

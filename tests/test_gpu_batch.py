@@ -45,7 +45,8 @@ def _pack_exact(ccm, arr):
     return ccm.pack(to_dev(arr))
 
 
-def test_batch_matches_oracle(ccm):
+@pytest.mark.parametrize("slots,unit_segments", [(2, 64), (4, 64), (4, 4096)])
+def test_batch_matches_oracle(ccm, slots, unit_segments):
     from paper_1303_0270_gb300.batch import BatchMatvec
     mats, xs = _batch_inputs(77, 160)
     # degenerate shapes: short rows, a single field, rows of exactly 32 and 33 fields
@@ -55,7 +56,8 @@ def test_batch_matches_oracle(ccm):
         xs.append(synth.uniform_signed(950 + k, 0, c, 8).reshape(-1, 1))
     pa = [_pack_exact(ccm, a) for a in mats]
     px = [_pack_exact(ccm, x) for x in xs]
-    bm = BatchMatvec(pa, px, unit_segments=64)
+    bm = BatchMatvec(pa, px, unit_segments=unit_segments)
+    bm.slots = slots  # ring depth: 1 or 3 chunks in flight per warp
     bm.launch()
     torch.cuda.synchronize()
     for i, (a, x) in enumerate(zip(mats, xs)):

@@ -515,6 +515,21 @@ def test_matmul_tensor_worst_case_sums(ccm):
     assert np.array_equal(got[rows], expect)
 
 
+@pytest.mark.parametrize("b", [4, 8, 12, 16])
+@pytest.mark.parametrize("m,k,n", [(130, 264, 72), (64, 512, 136)])
+def test_matmul_tensor_unsigned_nibble_fields(ccm, m, k, n, b):
+    """Unsigned fields of exactly 4L bits (the digit planes read straight
+    from the stream's nibbles, the top digit unsigned), with the range ends
+    present, and a signed B against an unsigned A."""
+    a = _rand(m * 3 + b, (m, k), b, signed=False)
+    bm = _rand(n * 5 + b, (k, n), b, signed=b != 8)
+    o = oracle.matmul(oracle.pack(a), oracle.pack(bm))
+    pa, pb = ccm.pack(to_dev(a)), ccm.pack(to_dev(bm))
+    assert (pa.width, pa.is_signed) == (b, 0)
+    c = ccm.matmul(pa, pb, path=ccm.MATMUL_TENSOR, capacity=ccm.words_for(m, n, 64))
+    assert_same_packed(c, o, f"tensor matmul unsigned {m}x{k}x{n} b={b}")
+
+
 def test_matmul_tensor_class_sums_cross_2_23(ccm):
     """Mixed-sign digits whose class sums rise above 2^23 within K and come
     back down: P = 32767 has digits (15, 15, 15, 7), N = -32753 has digits
