@@ -41,6 +41,12 @@ void run_scale(const ccm_matrix& a, int64_t s, const ccm_matrix& c, void* ws, si
 // kernel has already merged the width statistics into out's header.
 void run_pack_scratch(const int64_t* vals, const ccm_matrix& out, cudaStream_t st,
                       bool stats_done = false);
+// The same from an int32 scratch whose width statistics the producing kernel
+// has already merged into out's header.
+void run_pack_scratch32(const int32_t* vals, const ccm_matrix& out, cudaStream_t st);
+// The tensor matmul writes C as int32 when the output capacity bounds C's
+// width by 31 bits (every result the output can hold fits int32).
+bool matmul_c32(const ccm_matrix& c);
 
 // Host checks of ccm_matvec that need no workspace (pointers, alignment,
 // shapes, y's minimum capacity).

@@ -205,7 +205,10 @@ int run_matmul(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c, in
       size_t c_bytes = ((m * n * sizeof(int64_t)) + 255) & ~(size_t)255;
       int rc = run_matmul_tc(a, b, c, cs, (char*)ws + c_bytes, st);
       if (rc != CCM_OK) return rc;
-      run_pack_scratch(cs, c, st, /*stats_done=*/true);
+      if (matmul_c32(c))
+        run_pack_scratch32(reinterpret_cast<const int32_t*>(cs), c, st);
+      else
+        run_pack_scratch(cs, c, st, /*stats_done=*/true);
       return CCM_OK;
     } else {
       const int ba = width_bound(a.capacity, m * k), bb = width_bound(b.capacity, k * n);

@@ -392,6 +392,7 @@ struct MmArgs {
   uint32_t b_rows_pad;  // rows per B digit plane (n_pad)
   uint32_t tiles_n;     // n_pad / bn
   int L;
+  int c32;              // 1: C is written as int32 (the output capacity bounds its width by 31)
 };
 
 template <int L>
@@ -526,10 +527,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint64_t col = (uint64_t)tn * BN + col0;
       if (row < args.m) {
         int64_t* dst = args.c + row * args.n + col;
+        int32_t* dst32 = reinterpret_cast<int32_t*>(args.c) + row * args.n + col;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           if (col + j < args.n) {
-            dst[j] = acc[j];
+            if (args.c32)
+              dst32[j] = (int32_t)acc[j];  // (statistics from the exact value below)
+            else
+              dst[j] = acc[j];
             orv |= fold(acc[j]);
             neg |= (uint32_t)(acc[j] < 0);
           }
@@ -605,6 +610,8 @@ int digits_for(int bmax) { return (bmax + 3) / 4; }
 
 // The tensor path needs both widths bounded by 16 bits (at most 4 digits) and
 // every class sum below 2^24.
+bool matmul_c32(const ccm_matrix& c) { return width_bound(c.capacity, c.rows * c.cols) <= 31; }
+
 bool matmul_tc_supported(const ccm_matrix& a, const ccm_matrix& b) {
   const uint64_t m = a.rows, k = a.cols, n = b.cols;
   if (!m || !n || !k) return false;
@@ -666,7 +673,8 @@ int run_matmul_tc(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c,
       !tc::make_map(&tb, pb, p.k_pad, (uint64_t)L * p.n_pad, (uint32_t)g.bn))
     return CCM_E_CUDA;
   tc::MmArgs args{c.hdr, c_scratch, m, n, (uint32_t)(p.k_pad / tc::kBK), (uint32_t)p.m_pad,
-                  (uint32_t)p.n_pad, (uint32_t)(p.n_pad / g.bn), L};
+                  (uint32_t)p.n_pad, (uint32_t)(p.n_pad / g.bn), L,
+                  matmul_c32(c) ? 1 : 0};
   const unsigned grid = (unsigned)((p.m_pad / tc::kBM) * (p.n_pad / g.bn));
   profile_begin(st);
   switch (L) {

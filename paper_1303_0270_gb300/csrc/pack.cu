@@ -420,6 +420,24 @@ void run_scale(const ccm_matrix& a, int64_t s, const ccm_matrix& c, void* /*ws*/
   profile_end(st);
 }
 
+void run_pack_scratch32(const int32_t* vals, const ccm_matrix& out, cudaStream_t st) {
+  const uint64_t n = out.rows * out.cols;
+  const int cls = ew_class(width_bound(out.capacity, n));
+  if (cls && n) {
+    ge::EwCall c{};
+    c.kind = ge::EwKind::PackI32;
+    c.dense = vals;
+    c.out = out.hdr;
+    c.words = out.words;
+    c.capacity = out.capacity;
+    c.rows = out.rows;
+    c.cols = out.cols;
+    launch_ew(cls, c, st);
+    return;
+  }
+  launch_pack(ProdDenseI32{vals}, out.hdr, out.words, out.capacity, n, st);
+}
+
 // Pack an int64 result held in device scratch (matvec / matmul epilogue).
 void run_pack_scratch(const int64_t* vals, const ccm_matrix& out, cudaStream_t st,
                       bool stats_done) {

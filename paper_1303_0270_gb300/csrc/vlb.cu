@@ -13,7 +13,8 @@
 //                memory, interior words stored, the two boundary words OR-ed
 // -- and it also writes an index: the bit offset of every 64th entry (plus
 // the total), which lets the decoder k_vlb_unpack run one thread per 64
-// entries.  The index is this library's addition (the paper has none).
+// entries (a warp's 32 x 64 values staged in shared memory and stored
+// coalesced).  The index is this library's addition (the paper has none).
 #include "ccm_device.cuh"
 #include "kernels.h"
 #include "pack_engine.cuh"
@@ -276,31 +277,64 @@ __device__ __forceinline__ int check_vlb(const ccm_header* hdr, uint64_t rows, u
   return CCM_OK;
 }
 
+// Decode: thread c walks the 64 entries of index chunk c from their indexed
+// bit offset (prefix, then value).  The 32 lanes of a warp hold 32
+// consecutive chunks; each lane decodes its chunk in two halves of 32
+// entries, staged in shared memory (33 slots per lane) and then stored by the
+// warp one chunk-half at a time with consecutive lanes on consecutive entries
+// (coalesced 128- or 256-byte runs), only the entries a lane decoded.
+constexpr int kUnpackWarps = 8;
+constexpr int kHalf = kStride / 2;
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_vlb_unpack(const ccm_header* hdr,
-                                                    const uint32_t* __restrict__ words,
-                                                    const uint64_t* __restrict__ index,
-                                                    uint64_t rows, uint64_t cols, uint64_t capacity,
-                                                    T* __restrict__ out, int32_t* err) {
+__global__ void __launch_bounds__(kUnpackWarps * 32) k_vlb_unpack(
+    const ccm_header* hdr, const uint32_t* __restrict__ words, const uint64_t* __restrict__ index,
+    uint64_t rows, uint64_t cols, uint64_t capacity, T* __restrict__ out, int32_t* err) {
+  extern __shared__ __align__(16) uint8_t s_raw[];
+  T* stage = reinterpret_cast<T*>(s_raw) + (threadIdx.x / 32) * 32 * (kHalf + 1);
   const uint64_t n = rows * cols;
   int st = check_vlb(hdr, rows, cols, capacity);
   if (st == CCM_OK && sizeof(T) == 4 && (int)hdr->reserved0 > 31) st = CCM_E_WIDTH;
   if (err && blockIdx.x == 0 && threadIdx.x == 0) *err = st;
   if (st != CCM_OK) return;
   const int k = hdr->width;
+  const uint64_t limit = hdr->stat_or;  // total bits: never read past the stream
   const uint64_t chunks = (n + kStride - 1) / kStride;
-  for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < chunks;
-       c += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t pos = index[c];
-    const uint64_t limit = hdr->stat_or;  // total bits: never read past the stream
-    const uint64_t e_end = umin(n, (c + 1) * kStride);
+  const int lane = threadIdx.x % 32;
+  const uint64_t nwarps = (uint64_t)gridDim.x * kUnpackWarps;
+  T* mine = stage + lane * (kHalf + 1);
+  for (uint64_t wc = (uint64_t)blockIdx.x * kUnpackWarps + threadIdx.x / 32; wc * 32 < chunks;
+       wc += nwarps) {
+    const uint64_t c = wc * 32 + lane;
+    const int e_cnt = c < chunks ? (int)umin(kStride, n - c * kStride) : 0;
+    uint64_t pos = c < chunks ? index[c] : 0;
     BitReader br(words, pos);
-    for (uint64_t e = c * kStride; e < e_end; ++e) {
-      if (pos + k > limit) break;
-      const int L = (int)br.take(k);
-      if (L < 1 || L > 64 || pos + k + L > limit) break;
-      out[e] = (T)br.take64(L);
-      pos += k + L;
+    bool ok = true;
+    const uint64_t e0 = wc * 32 * kStride;
+    for (int h = 0; h < 2; ++h) {
+      int cnt = 0;  // entries of this half the lane decoded
+      for (; ok && cnt < kHalf && h * kHalf + cnt < e_cnt; ++cnt) {
+        if (pos + k > limit) {
+          ok = false;
+          break;
+        }
+        const int L = (int)br.take(k);
+        if (L < 1 || L > 64 || pos + k + L > limit) {
+          ok = false;
+          break;
+        }
+        mine[cnt] = (T)br.take64(L);
+        pos += k + L;
+      }
+      __syncwarp();
+      // chunk-half by chunk-half: lane j stores entry j of the owner's half
+#pragma unroll 4
+      for (int owner = 0; owner < 32; ++owner) {
+        const int oc = __shfl_sync(0xffffffffu, cnt, owner);
+        const uint64_t e = e0 + (uint64_t)owner * kStride + h * kHalf + lane;
+        if (lane < oc) out[e] = stage[owner * (kHalf + 1) + lane];
+      }
+      __syncwarp();
     }
   }
 }
@@ -421,14 +455,27 @@ void run_vlb_unpack(const ccm_header* hdr, const uint32_t* words, uint64_t capac
                     int32_t* err, cudaStream_t st) {
   const uint64_t n = rows * cols;
   const uint64_t chunks = (n + vlb::kStride - 1) / vlb::kStride;
-  const int g = (int)umin(umax((chunks + 255) / 256, 1), (uint64_t)num_sms() * 8);
+  const uint64_t warp_groups = (chunks + 31) / 32;
+  const int g = (int)umin(umax((warp_groups + vlb::kUnpackWarps - 1) / vlb::kUnpackWarps, 1),
+                          (uint64_t)num_sms() * 8);
+  const int threads = vlb::kUnpackWarps * 32;
+  const size_t per = (size_t)vlb::kUnpackWarps * 32 * (vlb::kHalf + 1);
   profile_begin(st);
-  if (dtype == CCM_I64)
-    vlb::k_vlb_unpack<int64_t><<<g, 256, 0, st>>>(hdr, words, index, rows, cols, capacity,
-                                                   (int64_t*)dense, err);
-  else
-    vlb::k_vlb_unpack<int32_t><<<g, 256, 0, st>>>(hdr, words, index, rows, cols, capacity,
-                                                   (int32_t*)dense, err);
+  if (dtype == CCM_I64) {
+    static int attr_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_dev != dev) {
+      cudaFuncSetAttribute(vlb::k_vlb_unpack<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(per * sizeof(int64_t)));
+      attr_dev = dev;
+    }
+    vlb::k_vlb_unpack<int64_t><<<g, threads, per * sizeof(int64_t), st>>>(
+        hdr, words, index, rows, cols, capacity, (int64_t*)dense, err);
+  } else {
+    vlb::k_vlb_unpack<int32_t><<<g, threads, per * sizeof(int32_t), st>>>(
+        hdr, words, index, rows, cols, capacity, (int32_t*)dense, err);
+  }
   profile_end(st);
   note_launch();
 }
