@@ -474,7 +474,8 @@ def batch_measure(torch, ccm, dev, count, seed, steps, warmup):
     return {"workload": f"{count} packed matrices, rows/cols log-uniform [16, 2048), "
                         "widths U{1..24}, signed uniform values, x signed 8-bit",
             "packed_bytes": packed_bytes, "fields": int((rows * cols).sum()),
-            "autotune": {k: tune[k] for k in ("unit_segments", "grid", "slots") if k in tune},
+            "autotune": {k: tune[k] for k in ("unit_segments", "grid", "slots", "stage_bytes")
+                         if k in tune},
             "ms": round(ms_batch, 4), "GB/s": round(gbs, 2), "frac_of_hbm": round(gbs / hbm, 4),
             "plain_ms": round(ms_plain, 3), "speedup_vs_plain": round(ms_plain / ms_batch, 2),
             "mismatches_vs_plain": bad, "timing": f"mean of {steps} graph replays, CUDA events"}

@@ -92,7 +92,8 @@ typedef struct ccm_header {
   uint32_t stat_neg;  /* internal: 1 when some entry of the result is negative */
   uint32_t reserved0;  /* internal (VLB: the largest entry bit length; add/scale written
                           by the lane pass: the width that pass wrote) */
-  uint64_t reserved1;  /* internal (1: an add/scale was written by its lane pass) */
+  uint64_t reserved1;  /* internal (1: an add/scale was written by its lane pass; pack: a
+                          tile reached the width the capacity bounds) */
 } ccm_header;
 
 /* Host-side handle of one packed matrix: where it lives and its shape.
@@ -293,16 +294,22 @@ ccm_status ccm_repack(const ccm_matrix* in, int width, int is_signed, const ccm_
  * the plan: the buffers must stay where they are while the plan is used.
  *
  * ccm_batch_matvec launches an initialisation kernel (validates the headers,
- * clears y headers and the scratch) and the persistent kernel (`grid` CTAs;
- * <= 0 picks 3 per SM).  The initialisation kernel (one block per entry)
- * also decodes every x into an int32 image in `ws`; the main kernel's shared
- * memory holds each warp's info->slots staging slots for A widths up to
- * info->max_width (an info with max_width outside 1..32 or max_cols above
- * 8192, or slots other than 0, 2 or 4, or slots whose shared memory exceeds the
- * device's: CCM_E_INVAL).  `ws` is device workspace of at least
+ * clears y headers and the scratch, decodes every x into an image in `ws`:
+ * bytes when x fits 8 signed or 7 unsigned bits and width(A) <= 24, else
+ * int32), a one-CTA kernel that orders the valid entries' units by width and
+ * sign, and the persistent kernel (`grid` CTAs; <= 0 picks one resident
+ * wave).  Each warp of the persistent kernel takes work units in that order
+ * from an atomic ticket and streams their words through info->slots ring slots in shared
+ * memory, each stage one bulk copy of about info->stage_bytes bytes (the
+ * segments per lane follow from the width).  The slots are sized for A widths
+ * up to info->max_width.  An info with max_width outside 1..32 or max_cols
+ * above 8192, slots other than 0 (= 3) or 2..4, stage_bytes other than 0
+ * (= 3072) or 128..16384, or a ring whose shared memory exceeds the
+ * device's: CCM_E_INVAL.  `ws` is device workspace of at least
  * ccm_batch_workspace_bytes(...) bytes, 256-byte aligned.  Each y_i header
- * receives its own status.  Both launches are stream-ordered and can be
- * captured in a CUDA graph. */
+ * receives its own status (CCM_E_TIMEOUT if a bounded wait on a copy gave
+ * up).  The three launches are stream-ordered and can be captured in a CUDA
+ * graph. */
 typedef struct ccm_batch_entry {
   ccm_matrix a; /* m x n */
   ccm_matrix x; /* n x 1 */
@@ -317,9 +324,12 @@ typedef struct ccm_batch_info {
   uint32_t max_cols;      /* widest entry (at most 8192 columns) */
   uint64_t plan_bytes;
   uint32_t max_width;     /* widest A the capacities admit, <= 32 (sizes the staging) */
-  uint32_t slots;         /* ring slots per warp, 2 or 4 (set by the plan to 2; the caller
-                             may set 4 before ccm_batch_matvec: three chunks in flight) */
+  uint32_t slots;         /* ring slots per warp: 0 (default 3) or 2..4; set to 0 by the
+                             plan, the caller may change it before ccm_batch_matvec */
   uint64_t x_ints;        /* ints of the decoded-x images in the workspace */
+  uint32_t stage_bytes;   /* bytes of A per warp stage: 0 (default 3072) or 128..16384;
+                             set to 0 by the plan, the caller may change it */
+  uint32_t reserved;      /* 0 */
 } ccm_batch_info;
 
 size_t ccm_batch_plan_bytes(const ccm_batch_entry* entries, int count, uint32_t unit_segments);

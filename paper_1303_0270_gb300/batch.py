@@ -1,7 +1,8 @@
 """Batched matvec: thousands of packed matrices of uneven shapes and widths
 in one persistent launch (C ABI: ccm_batch_plan / ccm_batch_matvec), with an
-autotuner for the work-unit size and the persistent grid, and CUDA-graph
-replay.  Argument marshalling and orchestration only: the arithmetic runs in
+autotuner for the work-unit size, the ring depth and the stage size (which
+sets how many segments of 32 fields each lane decodes per stage), and
+CUDA-graph replay.  Argument marshalling and orchestration only: the arithmetic runs in
 libccm's kernels."""
 from __future__ import annotations
 
@@ -35,7 +36,8 @@ class BatchMatvec:
             self.entries[i].a, self.entries[i].x, self.entries[i].y = a.c(), x.c(), y.c()
         self.count = n
         self.grid = grid
-        self.slots = 2  # ring slots per warp (2 or 4)
+        self.slots = 0  # ring slots per warp (0 = the library's default, else 2..4)
+        self.stage_bytes = 0  # bytes of A per warp stage (0 = the library's default)
         self.graph = None
         L = ccm.lib()
         ws = L.ccm_batch_workspace_bytes(self.entries, n)
@@ -59,6 +61,7 @@ class BatchMatvec:
     def launch(self, stream=None):
         """Both launches of one batched matvec, asynchronous."""
         self.info.slots = self.slots
+        self.info.stage_bytes = self.stage_bytes
         ccm._check(ccm.lib().ccm_batch_matvec(
             ctypes.c_void_p(self.plan.data_ptr()), ctypes.byref(self.info),
             ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(), int(self.grid),
@@ -96,8 +99,8 @@ class BatchMatvec:
         return h.hexdigest()[:24]
 
     def autotune(self, candidates=None, reps: int = 3, cache: str | None = None):
-        """Time each (unit_segments, grid, ring slots) candidate on this batch
-        and keep the fastest; results are cached by batch signature (in memory and, when
+        """Time each (unit_segments, grid, ring slots, stage bytes) candidate
+        on this batch and keep the fastest; results are cached by batch signature (in memory and, when
         `cache` or $CCM_AUTOTUNE_CACHE names a file, on disk)."""
         cache = cache or os.environ.get("CCM_AUTOTUNE_CACHE")
         key = self.signature()
@@ -108,25 +111,27 @@ class BatchMatvec:
         if key in store:
             us, grid = store[key]["unit_segments"], store[key]["grid"]
             self.grid = grid
-            self.slots = store[key].get("slots", 2)
+            self.slots = store[key].get("slots", 0)
+            self.stage_bytes = store[key].get("stage_bytes", 0)
             if us != self.unit_segments:
                 self.set_unit_segments(us)
             return store[key]
-        sms = torch.cuda.get_device_properties(self.device).multi_processor_count
         if candidates is None:
-            # work-unit size x persistent grid x ring depth (chunks of 32
-            # segments, one segment of 32 fields per lane, in flight per warp)
-            candidates = [(us, g * sms, k) for us in (512, 1024, 2048, 4096)
-                          for g in (1, 2, 3, 4) for k in (2, 4)]
+            # work-unit size x ring depth x stage bytes (segments per lane
+            # per stage: about stage_bytes / (128 b)), one resident wave
+            candidates = [(us, 0, k, sb) for us in (256, 1024, 4096) for k in (2, 3, 4)
+                          for sb in (768, 1536, 3072)]
         best = None
         results = []
         for cand in candidates:
             us, grid = cand[0], cand[1]
-            slots = cand[2] if len(cand) > 2 else 2
+            slots = cand[2] if len(cand) > 2 else 0
+            stage = cand[3] if len(cand) > 3 else 0
             if us != self.unit_segments or self.plan is None:
                 self.set_unit_segments(us)
             self.grid = grid
             self.slots = slots
+            self.stage_bytes = stage
             try:
                 self.launch()
             except ccm.CCMError:
@@ -143,12 +148,15 @@ class BatchMatvec:
                 e1.synchronize()
                 times.append(e0.elapsed_time(e1))
             t = min(times)
-            results.append({"unit_segments": us, "grid": grid, "slots": slots, "ms": t})
+            res = {"unit_segments": us, "grid": grid, "slots": slots, "stage_bytes": stage,
+                   "ms": t}
+            results.append(res)
             if best is None or t < best["ms"]:
-                best = {"unit_segments": us, "grid": grid, "slots": slots, "ms": t}
+                best = dict(res)
         self.set_unit_segments(best["unit_segments"])
         self.grid = best["grid"]
         self.slots = best["slots"]
+        self.stage_bytes = best["stage_bytes"]
         best["tried"] = results
         store[key] = best
         if cache:

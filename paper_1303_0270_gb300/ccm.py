@@ -55,7 +55,8 @@ class BatchInfo(ctypes.Structure):
                 ("y_rows", ctypes.c_uint64), ("unit_segments", ctypes.c_uint32),
                 ("max_cols", ctypes.c_uint32), ("plan_bytes", ctypes.c_uint64),
                 ("max_width", ctypes.c_uint32), ("slots", ctypes.c_uint32),
-                ("x_ints", ctypes.c_uint64)]
+                ("x_ints", ctypes.c_uint64), ("stage_bytes", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 assert ctypes.sizeof(Header) == 64

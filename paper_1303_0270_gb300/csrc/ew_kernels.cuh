@@ -830,12 +830,33 @@ __global__ void __launch_bounds__(kThreads) k_pack_dense(const T* __restrict__ s
 // Since the matrix width is the largest tile width, b_loc <= b and every
 // slot fits.  k_repack then re-codes each slot from b_loc to b (packed bytes
 // only, mostly from L2).  Dense traffic: one read instead of two.
+//
+// Speculative width: the output's capacity bounds b by b_spec (the widest
+// width whose words fit).  With b_spec given, every tile is also packed at
+// b_spec straight into its final place in the output; if the matrix width
+// turns out to be b_spec -- certain as soon as one tile's own width is
+// b_spec -- the output is complete after this one pass and k_repack only
+// writes the header.  A tile whose width is b_spec sets a flag in the output
+// header (reserved1); tiles that see the flag skip their workspace slot,
+// which only a narrower matrix needs.  Without the flag every tile keeps
+// its slot, so a narrower matrix is re-coded from the slots as above.
 // ---------------------------------------------------------------------------
 // Dense int64 tiles are double-buffered with 16-byte cp.async (zero fill past
 // the end): the next tile is in flight while the warp packs the current one.
 // Shared layout: element f at f + 2*(f/32) (keeps 16-byte alignment; the
 // lane's 16-byte reads of its 32 elements are conflict-free).
 constexpr int kDensePad = kTile + 2 * (kTile / 32);  // int64 slots per staged tile
+
+// Relaxed loads and stores at GPU scope (the speculation flag: written by
+// some warps, read by all; no ordering needed beyond eventual visibility).
+__device__ __forceinline__ uint64_t ld_relaxed_gpu(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];\n" : "=l"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_gpu(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;\n" ::"l"(p), "l"(v));
+}
 
 __device__ __forceinline__ void issue_dense_tile(int64_t* dst, const int64_t* __restrict__ src,
                                                  uint64_t base, uint32_t nt, int lane) {
@@ -853,7 +874,8 @@ __global__ void __launch_bounds__(kThreads) k_pack_local(const T* __restrict__ s
                                                          uint32_t* __restrict__ slots,
                                                          uint32_t slot_words,
                                                          uint8_t* __restrict__ tile_width,
-                                                         uint64_t n) {
+                                                         uint64_t n, uint32_t* words,
+                                                         int b_spec) {
   constexpr bool kPipe = sizeof(T) == 8;
   constexpr int kStageWords = kPipe ? 2 * kDensePad : kBufWords;  // uint32 words per buffer
   // dynamic: kWarps x (2 buffers for int64, 1 for int32) x kStageWords words
@@ -873,8 +895,13 @@ __global__ void __launch_bounds__(kThreads) k_pack_local(const T* __restrict__ s
                        tile * kTile, (uint32_t)umin((uint64_t)kTile, n - tile * kTile), lane);
     cp_async_commit_ge();
   }
+  // the speculation flag as this warp last saw it (sticky once set, so a
+  // warp stops reading it after the first time it finds it set)
+  bool known = false;
   for (; tile < ntiles; tile += gwarps) {
     const uint32_t nt = (uint32_t)umin((uint64_t)kTile, n - tile * kTile);
+    // (read before the tile's wait so that its latency hides behind it)
+    if (b_spec && !known) known = ld_relaxed_gpu(&out->reserved1) != 0;
     int64_t v[32];
     uint32_t* buf;  // where the packed words are staged
     if constexpr (kPipe) {
@@ -918,18 +945,39 @@ __global__ void __launch_bounds__(kThreads) k_pack_local(const T* __restrict__ s
     g_neg |= neg;
     const int bl = width_from_stats(orv, neg);
     const bool fits = bl <= BMAX && 32 * bl <= (int)slot_words;
-    if (fits) {
-      uint32_t u[32];
-      const uint32_t mask = bl >= 32 ? 0xffffffffu : ((1u << bl) - 1u);
+    // the slot is needed unless the matrix width is known to be b_spec
+    bool slot = true;
+    if (b_spec) {
+      if (bl == b_spec && !known && lane == 0) st_relaxed_gpu(&out->reserved1, 1ull);
+      slot = !(known || bl == b_spec);
+      known = known || bl == b_spec;
+    }
+    // up to two encodes of the tile, one code path: at b_spec into the
+    // output, then at b_loc into the slot (b_loc <= b_spec, so masking the
+    // same registers again only narrows them)
+    uint32_t u[32];
 #pragma unroll
-      for (int k = 0; k < 32; ++k) u[k] = (uint32_t)v[k] & mask;
-      encode_dispatch<BMAX>(bl, u, buf, lane);
+    for (int k = 0; k < 32; ++k) u[k] = (uint32_t)v[k];
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+      const int w = pass == 0 ? b_spec : bl;
+      if (pass == 0 ? !(b_spec && bl <= b_spec) : !(fits && slot)) continue;
+      const uint32_t mask = w >= 32 ? 0xffffffffu : ((1u << w) - 1u);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) u[k] &= mask;
+      encode_dispatch<BMAX>(w, u, buf, lane);
       __syncwarp();
-      uint4* dst = reinterpret_cast<uint4*>(slots + tile * (uint64_t)slot_words);
-      for (int q = lane; q < 8 * bl; q += 32) {
-        const int w = 4 * q;
-        dst[q] = make_uint4(buf[stage_pos(w, bl)], buf[stage_pos(w + 1, bl)],
-                            buf[stage_pos(w + 2, bl)], buf[stage_pos(w + 3, bl)]);
+      if (pass == 0) {
+        // the tile at b_spec in its final place (the low b_spec bits of a
+        // value that fits b_spec bits, signed or not)
+        store_packed(buf, words, tile, w, data_words(n, w), lane);
+      } else {
+        uint4* dst = reinterpret_cast<uint4*>(slots + tile * (uint64_t)slot_words);
+        for (int q = lane; q < 8 * w; q += 32) {
+          const int wq = 4 * q;
+          dst[q] = make_uint4(buf[stage_pos(wq, w)], buf[stage_pos(wq + 1, w)],
+                              buf[stage_pos(wq + 2, w)], buf[stage_pos(wq + 3, w)]);
+        }
       }
       __syncwarp();
     }
@@ -942,47 +990,97 @@ __global__ void __launch_bounds__(kThreads) k_pack_local(const T* __restrict__ s
   }
 }
 
+// k_repack: a warp takes K tiles at a time (tiles t, t + G, ..., G the
+// grid's warp count) and issues all their loads before it re-codes any: the
+// K width bytes first, then the K slots' words into registers, which go to K
+// staging areas of the warp's shared buffer; so a warp waits for two memory
+// round trips per K tiles instead of two per tile.  The re-code loop is not
+// unrolled (one copy of the width dispatch).
 template <int BMAX>
 __global__ void __launch_bounds__(kThreads) k_repack(const uint32_t* __restrict__ slots,
                                                      uint32_t slot_words,
                                                      const uint8_t* __restrict__ tile_width,
                                                      ccm_header* out, uint32_t* words,
-                                                     uint64_t capacity, uint64_t n) {
+                                                     uint64_t capacity, uint64_t n, int b_spec) {
+  constexpr int Q = (BMAX + 3) / 4;                        // uint4 per lane of a full slot
+  constexpr int K = BMAX <= 8 ? 4 : (BMAX <= 16 ? 2 : 1);  // tiles in flight per warp
+  constexpr int kArea = 33 * BMAX;                         // staged words of one tile
+  static_assert(K * kArea <= kBufWords, "staging areas exceed the warp's buffer");
   __shared__ __align__(16) uint32_t s_buf[kWarps][kBufWords];
+  ax::grid_dep_wait();  // (launched early: the local pass must have finished)
   int b, sgn;
-  if (!resolve_output(out, words, capacity, n, b, sgn)) return;  // also: a tile wider than BMAX
+  if (!resolve_output(out, words, capacity, n, b, sgn)) return;
+  if (b_spec && b == b_spec) return;  // k_pack_local wrote every tile at b
   const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
   uint32_t* buf = s_buf[warp];
   const uint64_t dw = data_words(n, b);
   const uint32_t mask = b >= 32 ? 0xffffffffu : ((1u << b) - 1u);
   const uint64_t ntiles = (n + kTile - 1) / kTile;
   const uint64_t gwarps = (uint64_t)gridDim.x * kWarps;
-  for (uint64_t tile = (uint64_t)blockIdx.x * kWarps + warp; tile < ntiles; tile += gwarps) {
-    const int tw = tile_width[tile];
-    const int bl = tw & 0x7f, sl = tw >> 7;
-    const uint4* src = reinterpret_cast<const uint4*>(slots + tile * (uint64_t)slot_words);
-    if (bl == b && tile * (uint64_t)(32 * b) + 32 * b <= dw) {
-      // the tile is already at the matrix width: its bits are final (a value
-      // that fits b bits has the same low b bits signed or unsigned)
-      uint4* dst = reinterpret_cast<uint4*>(words + tile * (uint64_t)(32 * b));
-      for (int q = lane; q < 8 * b; q += 32) dst[q] = __ldg(src + q);
-      continue;
+  for (uint64_t t0 = (uint64_t)blockIdx.x * kWarps + warp; t0 < ntiles; t0 += K * gwarps) {
+    int tw[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const uint64_t t = t0 + k * gwarps;
+      tw[k] = t < ntiles ? (int)tile_width[t] : 0;
     }
-    for (int q = lane; q < 8 * bl; q += 32) {
-      const uint4 v = __ldg(src + q);
-      const int w = 4 * q;
-      buf[stage_pos(w, bl)] = v.x;
-      buf[stage_pos(w + 1, bl)] = v.y;
-      buf[stage_pos(w + 2, bl)] = v.z;
-      buf[stage_pos(w + 3, bl)] = v.w;
+    uint4 r[K][Q];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const uint64_t t = t0 + k * gwarps;
+      const int bl = tw[k] & 0x7f;
+      const uint4* src = reinterpret_cast<const uint4*>(slots + t * (uint64_t)slot_words);
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        const int q = lane + 32 * j;
+        // (a tile wider than BMAX, width byte 0xFF, is never read)
+        r[k][j] = (t < ntiles && bl <= BMAX && q < 8 * bl) ? __ldg(src + q) : make_uint4(0, 0, 0, 0);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const uint64_t t = t0 + k * gwarps;
+      const int bl = tw[k] & 0x7f;
+      if (t >= ntiles || bl > BMAX) continue;
+      if (bl == b && t * (uint64_t)(32 * b) + 32 * b <= dw) {
+        // the tile is already at the matrix width: its bits are final (a value
+        // that fits b bits has the same low b bits signed or unsigned)
+        uint4* dst = reinterpret_cast<uint4*>(words + t * (uint64_t)(32 * b));
+#pragma unroll
+        for (int j = 0; j < Q; ++j)
+          if (lane + 32 * j < 8 * b) dst[lane + 32 * j] = r[k][j];
+        continue;
+      }
+      uint32_t* area = buf + k * kArea;
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        const int q = lane + 32 * j;
+        if (q < 8 * bl) {
+          const int w = 4 * q;
+          area[stage_pos(w, bl)] = r[k][j].x;
+          area[stage_pos(w + 1, bl)] = r[k][j].y;
+          area[stage_pos(w + 2, bl)] = r[k][j].z;
+          area[stage_pos(w + 3, bl)] = r[k][j].w;
+        }
+      }
     }
     __syncwarp();
-    uint32_t u[32];
-    decode_dispatch<BMAX>(bl, sl, buf, lane, [&](int k, int64_t x) { u[k] = (uint32_t)x & mask; });
-    __syncwarp();
-    encode_dispatch<BMAX>(b, u, buf, lane);
-    __syncwarp();
-    store_packed(buf, words, tile, b, dw, lane);
+#pragma unroll 1
+    for (int k = 0; k < K; ++k) {
+      const uint64_t t = t0 + k * gwarps;
+      const int twk = (int)tile_width[t < ntiles ? t : 0];  // (L1: read above)
+      const int bl = twk & 0x7f, sl = twk >> 7;
+      if (t >= ntiles || bl > BMAX) continue;
+      if (bl == b && t * (uint64_t)(32 * b) + 32 * b <= dw) continue;  // copied above
+      uint32_t* area = buf + k * kArea;
+      uint32_t u[32];
+      decode_dispatch<BMAX>(bl, sl, area, lane,
+                            [&](int f, int64_t x) { u[f] = (uint32_t)x & mask; });
+      __syncwarp();
+      encode_dispatch<BMAX>(b, u, area, lane);
+      __syncwarp();
+      store_packed(area, words, t, b, dw, lane);
+    }
     __syncwarp();
   }
 }
@@ -1050,7 +1148,8 @@ struct EwCall {
   int32_t* err;           // unpack status
   void* ws;               // Local* / Repack: workspace (slots, then tile widths)
   int slot_class;         // Local* / Repack: width class of the output (slot = 32*class words)
-  int spec;               // AddPack / ScalePack: an AddSpec / ScaleSpec launch came first
+  int spec;               // AddPack / ScalePack: an AddSpec / ScaleSpec launch came first;
+                          // LocalI64 / LocalI32 / Repack: the speculative width (0: none)
 };
 
 inline int ew_grid(uint64_t n, int per_sm) {
@@ -1144,14 +1243,17 @@ int launch_ew_pack(const EwCall& c, cudaStream_t st) {
           attr = true;
         }
         k_pack_local<int64_t, C><<<gl, kThreads, smem, st>>>((const int64_t*)c.dense, c.out,
-                                                             slots, slot_words, widths, n);
+                                                             slots, slot_words, widths, n,
+                                                             c.words, c.spec);
       } else if (c.kind == EwKind::LocalI32) {
         const size_t smem = (size_t)kWarps * kBufWords * sizeof(uint32_t);
         k_pack_local<int32_t, C><<<gl, kThreads, smem, st>>>((const int32_t*)c.dense, c.out,
-                                                             slots, slot_words, widths, n);
+                                                             slots, slot_words, widths, n,
+                                                             c.words, c.spec);
       } else {
-        k_repack<C><<<gl, kThreads, 0, st>>>(slots, slot_words, widths, c.out, c.words, c.capacity,
-                                             n);
+        ax::launch_pdl(k_repack<C>, dim3(gl), dim3(kThreads), 0, st, (const uint32_t*)slots,
+                       slot_words, (const uint8_t*)widths, c.out, c.words, c.capacity, n,
+                       c.spec);
       }
       break;
     }

@@ -179,6 +179,9 @@ void run_pack(const void* dense, int dtype, uint64_t rows, uint64_t cols, const 
     c.cols = cols;
     c.ws = ws;
     c.slot_class = cls;
+    // the widest width the output's capacity holds: the speculative width
+    c.spec = width_bound(out.capacity, n);
+    if (c.spec > cls) c.spec = 0;
     profile_begin(st);
     launch_ew(cls, c, st);
     profile_end(st);

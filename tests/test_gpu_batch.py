@@ -45,8 +45,9 @@ def _pack_exact(ccm, arr):
     return ccm.pack(to_dev(arr))
 
 
-@pytest.mark.parametrize("slots,unit_segments", [(2, 64), (4, 64), (4, 4096)])
-def test_batch_matches_oracle(ccm, slots, unit_segments):
+@pytest.mark.parametrize("slots,unit_segments,stage_bytes",
+                         [(2, 64, 0), (4, 64, 128), (3, 4096, 6144), (0, 1024, 1536)])
+def test_batch_matches_oracle(ccm, slots, unit_segments, stage_bytes):
     from paper_1303_0270_gb300.batch import BatchMatvec
     mats, xs = _batch_inputs(77, 160)
     # degenerate shapes: short rows, a single field, rows of exactly 32 and 33 fields
@@ -57,7 +58,8 @@ def test_batch_matches_oracle(ccm, slots, unit_segments):
     pa = [_pack_exact(ccm, a) for a in mats]
     px = [_pack_exact(ccm, x) for x in xs]
     bm = BatchMatvec(pa, px, unit_segments=unit_segments)
-    bm.slots = slots  # ring depth: 1 or 3 chunks in flight per warp
+    bm.slots = slots  # ring depth: 1 to 3 stages in flight per warp (0: the default)
+    bm.stage_bytes = stage_bytes  # 128: one segment per lane per stage; 6144: up to 8
     bm.launch()
     torch.cuda.synchronize()
     for i, (a, x) in enumerate(zip(mats, xs)):

@@ -280,6 +280,34 @@ def test_width_class_and_runtime_kernels_agree(ccm, b):
                                f"scale {s} b={b} cap={cap}")
 
 
+@pytest.mark.parametrize("b", [1, 3, 5, 8, 11, 16, 23, 30, 32])
+@pytest.mark.parametrize("case", ["first", "last", "over"])
+def test_pack_speculative_width(ccm, b, case):
+    """Single-pass pack when the output capacity bounds the width by exactly
+    the matrix width (the speculative width): the one entry that needs all b
+    bits sits in the first tile or in the last, every other tile is narrower,
+    so most tiles are packed before any has reached the speculative width.
+    'over': the capacity allows two bits more than the data needs, the
+    speculation misses and every tile is re-coded from its local-width slot.
+    Against the oracle word for word (padding included)."""
+    shape = (40, 1500)  # 60000 fields: 59 tiles, a ragged last one
+    signed = b % 2 == 1
+    v = _rand(31 * b + 7, shape, max(1, b - 1), signed)
+    extreme = synth.signed_range(b)[0] if signed else (1 << b) - 1
+    if case == "last":
+        v.flat[-3] = extreme
+    else:
+        v.flat[5] = extreme
+    cap_width = b + 2 if case == "over" else b
+    if cap_width > 32:
+        pytest.skip("a capacity above 32 bits takes the run-time-width kernels")
+    o = oracle.pack(v)
+    assert o.width == b
+    p = _pack_cap(ccm, v, cap_width)
+    assert_same_packed(p, o, f"speculative pack b={b} {case}")
+    assert np.array_equal(ccm.unpack(p).cpu().numpy(), v)
+
+
 @pytest.mark.parametrize("ba,sa,bb,sb", [(5, 0, 5, 0), (1, 0, 1, 0), (3, 0, 4, 0), (7, 0, 7, 0),
                                          (2, 0, 6, 0), (8, 0, 1, 0), (7, 1, 3, 0), (3, 0, 7, 1),
                                          (8, 1, 8, 1), (16, 1, 1, 0), (13, 0, 13, 0),
