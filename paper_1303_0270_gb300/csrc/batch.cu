@@ -500,6 +500,11 @@ __device__ __noinline__ void run_stage(uint32_t sp, uint64_t w_lo, uint32_t g0, 
                                        const int* ximg, int64_t* ys) {
   const int lane = threadIdx.x % 32;
   const uint32_t ds1 = ds & 255u, ds2 = ds >> 8;
+  // Fast path: each lane keeps a running sum for its current row and adds it
+  // to y (one atomic, no warp-wide step) when its next segment starts another
+  // row and at the end of the stage.  General path: rows reduced per sub-step.
+  int64_t racc = 0;
+  uint32_t rrow = 0xffffffffu;
   for (uint32_t base = g0; base < g1; base += 32) {
     const uint32_t g = base + lane;
     const bool live = g < g1;
@@ -508,7 +513,6 @@ __device__ __noinline__ void run_stage(uint32_t sp, uint64_t w_lo, uint32_t g0, 
     const uint32_t s = gg - q * nsr;
     const uint64_t bit = ((uint64_t)q * n + 32u * s) * (uint64_t)B;
     const uint32_t wo = (uint32_t)((bit >> 5) - w_lo), sh = (uint32_t)bit & 31u;
-    int64_t acc;
     if constexpr (FAST) {
       const int4* xb = reinterpret_cast<const int4*>(ximg);
       const int4 x0 = __ldg(xb + s), x1 = __ldg(xb + nsr + s);
@@ -516,15 +520,25 @@ __device__ __noinline__ void run_stage(uint32_t sp, uint64_t w_lo, uint32_t g0, 
       uint32_t f[B + 1];
       load_segment<B>(sp, wo, sh, f);
       const int xw[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-      acc = seg_dot_fast<B, SGN>(f, xw, xs);
+      const int64_t acc = seg_dot_fast<B, SGN>(f, xw, xs);
+      if (live) {
+        if (q != rrow) {
+          if (racc) atomicAdd(reinterpret_cast<unsigned long long*>(ys + rrow), (unsigned long long)racc);
+          rrow = q;
+          racc = acc;
+        } else {
+          racc += acc;
+        }
+      }
     } else {
       uint32_t f[B + 1];
       load_segment<B>(sp, wo, sh, f);
-      acc = seg_dot_gen<B, SGN>(f, reinterpret_cast<const int4*>(ximg) + s, nsr);
+      int64_t acc = seg_dot_gen<B, SGN>(f, reinterpret_cast<const int4*>(ximg) + s, nsr);
+      if (!live) acc = 0;
+      row_add<FAST>(acc, live ? q : 0xffffffffu, nsr, ys, lane);
     }
-    if (!live) acc = 0;
-    row_add<FAST>(acc, live ? q : 0xffffffffu, nsr, ys, lane);
   }
+  if (FAST && racc) atomicAdd(reinterpret_cast<unsigned long long*>(ys + rrow), (unsigned long long)racc);
 }
 
 // Re-pack y of one matrix at its exact width; the whole warp takes part
