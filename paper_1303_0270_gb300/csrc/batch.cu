@@ -438,35 +438,12 @@ __device__ __forceinline__ int64_t seg_dot_gen(const uint32_t (&f)[B + 1], const
   return acc;
 }
 
-// Adds each lane's segment sum to its row of y.  The rows of a sub-step are
-// runs of consecutive lanes, each at most nsr long (a row has nsr segments).
-// Fast path (|acc| < 2^55): up to three rows -- always, when nsr >= 17 --
-// are summed one row at a time with two 32-bit redux.sync over the whole
-// warp (the other rows' lanes add zero); no shuffle.  Otherwise a segmented
-// shuffle reduction with as many steps as the longest run needs.
-template <bool FAST>
+// General path: adds each lane's segment sum to its row of y.  The rows of a
+// sub-step are runs of consecutive lanes, each at most nsr long (a row has
+// nsr segments): a segmented shuffle reduction with as many steps as the
+// longest run needs leaves each row's sum in its first lane.
 __device__ __forceinline__ void row_add(int64_t acc, uint32_t row, uint32_t nsr, int64_t* ys,
                                         int lane) {
-  const uint32_t r0 = __shfl_sync(0xffffffffu, row, 0);  // (lane 0 is always live)
-  if (FAST) {
-    const uint32_t rl = __reduce_max_sync(0xffffffffu, row == 0xffffffffu ? 0u : row);
-    const uint32_t nrows = rl - r0 + 1;
-    if (nrows <= 3) {
-      const uint32_t lo = (uint32_t)acc & 0xffffffu;
-      const int hi = (int)(acc >> 24);
-      for (uint32_t k = 0; k < nrows; ++k) {
-        const bool in = row == r0 + k;
-        const uint32_t l = __reduce_add_sync(0xffffffffu, in ? lo : 0u);
-        const int h = __reduce_add_sync(0xffffffffu, in ? hi : 0);
-        if (lane == 0) {
-          const int64_t v = (int64_t)h * (1 << 24) + (int64_t)l;
-          if (v) atomicAdd(reinterpret_cast<unsigned long long*>(ys + r0 + k), (unsigned long long)v);
-        }
-      }
-      return;
-    }
-  }
-  // segmented reduction by row: the first lane of each row gets the total
   const uint32_t span = nsr < 32 ? nsr : 32;
   long long s = acc;
   for (uint32_t d = 1; d < span; d <<= 1) {
@@ -535,7 +512,7 @@ __device__ __noinline__ void run_stage(uint32_t sp, uint64_t w_lo, uint32_t g0, 
       load_segment<B>(sp, wo, sh, f);
       int64_t acc = seg_dot_gen<B, SGN>(f, reinterpret_cast<const int4*>(ximg) + s, nsr);
       if (!live) acc = 0;
-      row_add<FAST>(acc, live ? q : 0xffffffffu, nsr, ys, lane);
+      row_add(acc, live ? q : 0xffffffffu, nsr, ys, lane);
     }
   }
   if (FAST && racc) atomicAdd(reinterpret_cast<unsigned long long*>(ys + rrow), (unsigned long long)racc);
