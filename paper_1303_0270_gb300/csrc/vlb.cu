@@ -303,15 +303,31 @@ __global__ void __launch_bounds__(kUnpackWarps * 32) k_vlb_unpack(
   const int lane = threadIdx.x % 32;
   const uint64_t nwarps = (uint64_t)gridDim.x * kUnpackWarps;
   T* mine = stage + lane * (kHalf + 1);
-  for (uint64_t wc = (uint64_t)blockIdx.x * kUnpackWarps + threadIdx.x / 32; wc * 32 < chunks;
-       wc += nwarps) {
+  uint64_t wc = (uint64_t)blockIdx.x * kUnpackWarps + threadIdx.x / 32;
+  // the bit offsets of the chunks of this warp's next group, loaded one group
+  // ahead (its decode hides their latency)
+  uint64_t npos = wc * 32 + lane < chunks ? __ldg(index + wc * 32 + lane) : 0;
+  for (; wc * 32 < chunks; wc += nwarps) {
     const uint64_t c = wc * 32 + lane;
     const int e_cnt = c < chunks ? (int)umin(kStride, n - c * kStride) : 0;
-    uint64_t pos = c < chunks ? index[c] : 0;
+    uint64_t pos = npos;
+    const uint64_t wn = wc + nwarps;
+    npos = wn * 32 + lane < chunks ? __ldg(index + wn * 32 + lane) : 0;
     BitReader br(words, pos);
     bool ok = true;
     const uint64_t e0 = wc * 32 * kStride;
     for (int h = 0; h < 2; ++h) {
+      if (h == 1 && wn * 32 < chunks) {
+        // the stream lines of the next group into L1 (its chunks are
+        // contiguous: from its first chunk's offset to past its last one's)
+        const uint64_t b0 = __shfl_sync(0xffffffffu, npos, 0);
+        const uint64_t cl = umin(chunks - wn * 32, 32) - 1;  // its last chunk (lane)
+        const uint64_t bl = __shfl_sync(0xffffffffu, npos, (int)cl);
+        const uint64_t l0 = b0 / 1024, l1 = umin((bl + (uint64_t)kStride * (k + 64)) / 1024,
+                                                 (limit + 1023) / 1024);
+        for (uint64_t ln = l0 + lane; ln < l1; ln += 32)
+          asm volatile("prefetch.global.L1 [%0];\n" ::"l"(words + ln * 32));
+      }
       int cnt = 0;  // entries of this half the lane decoded
       for (; ok && cnt < kHalf && h * kHalf + cnt < e_cnt; ++cnt) {
         if (pos + k > limit) {
