@@ -868,6 +868,20 @@ __device__ __forceinline__ void issue_dense_tile(int64_t* dst, const int64_t* __
   }
 }
 
+// The int32 form: element f at f + 4*(f/32) (16-byte aligned chunks of four;
+// a lane's 16-byte reads of its 32 elements are conflict-free).
+constexpr int kDensePad32 = kTile + 4 * (kTile / 32);  // int32 slots per staged tile
+
+__device__ __forceinline__ void issue_dense_tile(int32_t* dst, const int32_t* __restrict__ src,
+                                                 uint64_t base, uint32_t nt, int lane) {
+#pragma unroll 4
+  for (int j = 0; j < kTile / 4 / 32; ++j) {
+    const uint32_t f = 4 * (lane + 32 * j);
+    const uint32_t valid = f + 4 <= nt ? 16u : (f < nt ? 4u * (nt - f) : 0u);
+    cp_async16_zfill(dst + f + 4 * (f >> 5), src + base + (valid ? f : 0), valid);
+  }
+}
+
 template <typename T, int BMAX>
 __global__ void __launch_bounds__(kThreads) k_pack_local(const T* __restrict__ src,
                                                          ccm_header* out,
@@ -876,62 +890,65 @@ __global__ void __launch_bounds__(kThreads) k_pack_local(const T* __restrict__ s
                                                          uint8_t* __restrict__ tile_width,
                                                          uint64_t n, uint32_t* words,
                                                          int b_spec) {
-  constexpr bool kPipe = sizeof(T) == 8;
-  constexpr int kStageWords = kPipe ? 2 * kDensePad : kBufWords;  // uint32 words per buffer
-  // dynamic: kWarps x (2 buffers for int64, 1 for int32) x kStageWords words
+  // dynamic: kWarps x 2 buffers x kStageWords uint32 words
+  constexpr int kStageWords = sizeof(T) == 8 ? 2 * kDensePad : kDensePad32;
   extern __shared__ __align__(16) uint32_t s_dyn[];
   if (out->status != CCM_OK) return;
+  // b_spec < 0: the statistics are already in the header (an epilogue merged
+  // them): the width is exact and every tile goes straight to its place
+  const bool exact = b_spec < 0;
+  if (exact) b_spec = width_from_stats(out->stat_or, out->stat_neg);
   const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
-  uint32_t* buf0 = s_dyn + warp * (kPipe ? 2 * kStageWords : kBufWords);
+  uint32_t* buf0 = s_dyn + warp * 2 * kStageWords;
   const uint64_t ntiles = (n + kTile - 1) / kTile;
   const uint64_t gwarps = (uint64_t)gridDim.x * kWarps;
   uint64_t g_or = 0;
   uint32_t g_neg = 0;
   uint64_t tile = (uint64_t)blockIdx.x * kWarps + warp;
   int cur = 0;
-  if constexpr (kPipe) {
-    if (tile < ntiles)
-      issue_dense_tile(reinterpret_cast<int64_t*>(buf0), reinterpret_cast<const int64_t*>(src),
-                       tile * kTile, (uint32_t)umin((uint64_t)kTile, n - tile * kTile), lane);
-    cp_async_commit_ge();
-  }
+  if (tile < ntiles)
+    issue_dense_tile(reinterpret_cast<T*>(buf0), src, tile * kTile,
+                     (uint32_t)umin((uint64_t)kTile, n - tile * kTile), lane);
+  cp_async_commit_ge();
   // the speculation flag as this warp last saw it (sticky once set, so a
   // warp stops reading it after the first time it finds it set)
-  bool known = false;
+  bool known = exact;
   for (; tile < ntiles; tile += gwarps) {
     const uint32_t nt = (uint32_t)umin((uint64_t)kTile, n - tile * kTile);
     // (read before the tile's wait so that its latency hides behind it)
     if (b_spec && !known) known = ld_relaxed_gpu(&out->reserved1) != 0;
     int64_t v[32];
-    uint32_t* buf;  // where the packed words are staged
-    if constexpr (kPipe) {
+    {
       const uint64_t next = tile + gwarps;
       if (next < ntiles)
-        issue_dense_tile(reinterpret_cast<int64_t*>(buf0 + (cur ^ 1) * kStageWords),
-                         reinterpret_cast<const int64_t*>(src), next * kTile,
+        issue_dense_tile(reinterpret_cast<T*>(buf0 + (cur ^ 1) * kStageWords), src, next * kTile,
                          (uint32_t)umin((uint64_t)kTile, n - next * kTile), lane);
       cp_async_commit_ge();
       cp_async_wait1_ge();
       __syncwarp();
-      const int64_t* tb = reinterpret_cast<const int64_t*>(buf0 + cur * kStageWords);
+      if constexpr (sizeof(T) == 8) {
+        const int64_t* tb = reinterpret_cast<const int64_t*>(buf0 + cur * kStageWords);
 #pragma unroll
-      for (int k = 0; k < 32; k += 2) {
-        const longlong2 p = *reinterpret_cast<const longlong2*>(tb + 34 * lane + k);
-        v[k] = p.x;
-        v[k + 1] = p.y;
+        for (int k = 0; k < 32; k += 2) {
+          const longlong2 p = *reinterpret_cast<const longlong2*>(tb + 34 * lane + k);
+          v[k] = p.x;
+          v[k + 1] = p.y;
+        }
+      } else {
+        const int32_t* tb = reinterpret_cast<const int32_t*>(buf0 + cur * kStageWords);
+#pragma unroll
+        for (int k = 0; k < 32; k += 4) {
+          const int4 p = *reinterpret_cast<const int4*>(tb + 36 * lane + k);
+          v[k] = p.x;
+          v[k + 1] = p.y;
+          v[k + 2] = p.z;
+          v[k + 3] = p.w;
+        }
       }
       __syncwarp();
-      buf = buf0 + cur * kStageWords;  // the consumed tile's buffer stages the output
-      cur ^= 1;
-    } else {
-      T* tb = reinterpret_cast<T*>(buf0);
-      stage_dense<T>(tb, src, tile * kTile, nt, lane);
-      __syncwarp();
-#pragma unroll
-      for (int k = 0; k < 32; ++k) v[k] = (int64_t)tb[33 * lane + k];
-      __syncwarp();
-      buf = buf0;
     }
+    uint32_t* buf = buf0 + cur * kStageWords;  // the consumed tile's buffer stages the output
+    cur ^= 1;
     uint64_t orv = 0;
     uint32_t neg = 0;
 #pragma unroll
@@ -948,7 +965,7 @@ __global__ void __launch_bounds__(kThreads) k_pack_local(const T* __restrict__ s
     // the slot is needed unless the matrix width is known to be b_spec
     bool slot = true;
     if (b_spec) {
-      if (bl == b_spec && !known && lane == 0) st_relaxed_gpu(&out->reserved1, 1ull);
+      if (!exact && bl == b_spec && !known && lane == 0) st_relaxed_gpu(&out->reserved1, 1ull);
       slot = !(known || bl == b_spec);
       known = known || bl == b_spec;
     }
@@ -981,9 +998,9 @@ __global__ void __launch_bounds__(kThreads) k_pack_local(const T* __restrict__ s
       }
       __syncwarp();
     }
-    if (lane == 0) tile_width[tile] = fits ? (uint8_t)(bl | (neg ? 0x80 : 0)) : 0xFF;
+    if (lane == 0 && tile_width) tile_width[tile] = fits ? (uint8_t)(bl | (neg ? 0x80 : 0)) : 0xFF;
   }
-  if constexpr (kPipe) cp_async_wait0_ge();
+  cp_async_wait0_ge();
   if (lane == 0) {
     if (g_or) atomicOr(reinterpret_cast<unsigned long long*>(&out->stat_or), (unsigned long long)g_or);
     if (g_neg) atomicOr(&out->stat_neg, 1u);
@@ -1010,7 +1027,7 @@ __global__ void __launch_bounds__(kThreads) k_repack(const uint32_t* __restrict_
   ax::grid_dep_wait();  // (launched early: the local pass must have finished)
   int b, sgn;
   if (!resolve_output(out, words, capacity, n, b, sgn)) return;
-  if (b_spec && b == b_spec) return;  // k_pack_local wrote every tile at b
+  if (b_spec < 0 || (b_spec && b == b_spec)) return;  // k_pack_local wrote every tile at b
   const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
   uint32_t* buf = s_buf[warp];
   const uint64_t dw = data_words(n, b);
@@ -1231,8 +1248,10 @@ int launch_ew_pack(const EwCall& c, cudaStream_t st) {
       const uint64_t ntiles = (n + kTile - 1) / kTile;
       const int sc = c.slot_class;
       const uint32_t slot_words = (uint32_t)(32 * sc);
+      // (no workspace: the exact-width form, spec < 0, which needs neither)
       uint32_t* slots = (uint32_t*)c.ws;
-      uint8_t* widths = (uint8_t*)c.ws + ((ntiles * 32 * sc * 4 + 255) & ~(size_t)255);
+      uint8_t* widths =
+          c.ws ? (uint8_t*)c.ws + ((ntiles * 32 * sc * 4 + 255) & ~(size_t)255) : nullptr;
       const int gl = ew_grid(n, 12);
       if (c.kind == EwKind::LocalI64) {
         const size_t smem = (size_t)kWarps * 2 * 2 * kDensePad * sizeof(uint32_t);
@@ -1246,7 +1265,7 @@ int launch_ew_pack(const EwCall& c, cudaStream_t st) {
                                                              slots, slot_words, widths, n,
                                                              c.words, c.spec);
       } else if (c.kind == EwKind::LocalI32) {
-        const size_t smem = (size_t)kWarps * kBufWords * sizeof(uint32_t);
+        const size_t smem = (size_t)kWarps * 2 * kDensePad32 * sizeof(uint32_t);
         k_pack_local<int32_t, C><<<gl, kThreads, smem, st>>>((const int32_t*)c.dense, c.out,
                                                              slots, slot_words, widths, n,
                                                              c.words, c.spec);

@@ -167,7 +167,11 @@ void run_pack(const void* dense, int dtype, uint64_t rows, uint64_t cols, const 
   launch_init(ia, st);
   uint64_t n = rows * cols;
   const int cls = ew_class(width_bound(out.capacity, n));
-  if (cls && n && ws && ws_bytes >= ge::pack_ws_bytes(n, cls)) {
+  // (the single pass stages the dense tiles with 16-byte copies: it needs a
+  // 16-byte aligned input; an input aligned only to its element size takes
+  // the two-pass path below, which reads it element by element)
+  const bool aligned16 = reinterpret_cast<uintptr_t>(dense) % 16 == 0;
+  if (cls && n && ws && ws_bytes >= ge::pack_ws_bytes(n, cls) && aligned16) {
     // single pass over the dense input: local-width tiles, then re-code
     ge::EwCall c{};
     c.kind = dtype == CCM_I64 ? ge::EwKind::LocalI64 : ge::EwKind::LocalI32;
@@ -426,15 +430,21 @@ void run_scale(const ccm_matrix& a, int64_t s, const ccm_matrix& c, void* /*ws*/
 void run_pack_scratch32(const int32_t* vals, const ccm_matrix& out, cudaStream_t st) {
   const uint64_t n = out.rows * out.cols;
   const int cls = ew_class(width_bound(out.capacity, n));
-  if (cls && n) {
+  if (cls && n && reinterpret_cast<uintptr_t>(vals) % 16 == 0) {
+    // the producer merged the statistics: one pass at the exact width (the
+    // staged single-pass kernel, spec < 0), then the header
     ge::EwCall c{};
-    c.kind = ge::EwKind::PackI32;
+    c.kind = ge::EwKind::LocalI32;
     c.dense = vals;
     c.out = out.hdr;
     c.words = out.words;
     c.capacity = out.capacity;
     c.rows = out.rows;
     c.cols = out.cols;
+    c.slot_class = cls;
+    c.spec = -1;
+    launch_ew(cls, c, st);
+    c.kind = ge::EwKind::Repack;
     launch_ew(cls, c, st);
     return;
   }

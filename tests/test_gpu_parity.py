@@ -69,6 +69,24 @@ def test_pack_int32_input_and_degenerate(ccm):
     assert_same_packed(ccm.pack(to_dev(arr)), oracle.pack(arr), "word end")
 
 
+@pytest.mark.parametrize("dtype", [np.int64, np.int32])
+def test_pack_unaligned_dense_input(ccm, dtype):
+    """A dense input aligned only to its element size (a view one element into
+    a buffer): the single-pass pack stages 16-byte copies, so such an input
+    takes the element-wise path; the packed words are the same."""
+    rows, cols = 37, 1003  # 37111 fields: 37 tiles, a ragged last one
+    a = synth.uniform_signed(4242, 0, rows * cols, 9).reshape(rows, cols).astype(dtype)
+    flat = torch.empty(rows * cols + 1, dtype=torch.int64 if dtype == np.int64 else torch.int32,
+                       device=device())
+    flat[1:] = torch.from_numpy(a.ravel()).to(flat.device)
+    view = flat[1:].view(rows, cols)
+    assert view.data_ptr() % 16 != 0
+    o = oracle.pack(a.astype(np.int64))
+    p = ccm.pack_into(view, ccm.PackedMatrix(rows, cols, ccm.words_for(rows, cols, o.width),
+                                             device()))
+    assert_same_packed(p, o, f"unaligned {np.dtype(dtype).name} pack")
+
+
 def test_empty_matrix(ccm):
     dev = device()
     p = ccm.pack(torch.empty((0, 5), dtype=torch.int64, device=dev))
