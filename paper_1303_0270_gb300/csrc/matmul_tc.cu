@@ -158,7 +158,6 @@ __device__ void limbs_a_nibbles(const uint32_t* __restrict__ w, int sgn, uint64_
   const uint64_t plane = m_pad * k_pad;
   const uint32_t groups = (uint32_t)(k_pad / 8);
   for (uint64_t i = blockIdx.x; i < m_pad; i += gridDim.x) {
-#pragma unroll 4  // (several groups' loads in flight per thread)
     for (uint32_t q = threadIdx.x; q < groups; q += blockDim.x) {
       const uint64_t kk = 8ull * q;
       uint2 out[L];
@@ -212,37 +211,27 @@ __global__ void k_limbs_a(const ccm_header* out, const ccm_header* h, const uint
 }
 
 // B (k x n, row-major) -> planes [L][n_pad][k_pad] (transposed, K-major).
-// A CTA transposes tiles of 64 k x 128 n through shared memory (each thread
-// reads 32 consecutive fields of one row; 512 16-byte stores per digit
-// plane).  n_pad is a multiple of 64: the columns of a tile past n_pad are
-// not written.
-constexpr int kBtK = 64, kBtN = 128;
-
 __global__ void __launch_bounds__(256) k_limbs_bt(const ccm_header* out, const ccm_header* h,
                                                   const uint32_t* __restrict__ w, uint64_t k,
                                                   uint64_t n, uint64_t n_pad, uint64_t k_pad, int L,
                                                   uint8_t* __restrict__ planes) {
-  __shared__ uint8_t tile[4][kBtN][kBtK + 4];  // [digit][j][kk]
+  __shared__ uint8_t tile[4][32][64 + 4];  // [digit][j][kk]
   if (out->status != CCM_OK) return;
   const int b = h->width, sgn = h->is_signed;
   const uint64_t plane = n_pad * k_pad;
-  const uint64_t tiles_k = k_pad / kBtK, tiles_n = (n_pad + kBtN - 1) / kBtN;
+  const uint64_t tiles_k = k_pad / 64, tiles_n = n_pad / 32;
   // nibble-aligned fields (b = 4L <= 16) and rows of whole 8-field groups:
-  // thread t reads fields j = 32 (t % 4) .. + 31 of row kk = t / 4 of the tile
+  // thread t reads fields j = 8 (t % 4) .. + 7 of row kk = t / 4 of the tile
   const bool nib = b == 4 * L && L <= 4 && n % 8 == 0;
   for (uint64_t t = blockIdx.x; t < tiles_k * tiles_n; t += gridDim.x) {
-    const uint64_t k0 = (t % tiles_k) * kBtK, j0 = (t / tiles_k) * kBtN;
+    const uint64_t k0 = (t % tiles_k) * 64, j0 = (t / tiles_k) * 32;
     for (int l0 = 0; l0 < L; l0 += 4) {
       if (nib) {
-        const int kk = threadIdx.x / 4;
-        const uint64_t gk = k0 + kk;
-#pragma unroll 1
-        for (int g8 = 0; g8 < 4; ++g8) {
-          const int jg = 32 * (threadIdx.x % 4) + 8 * g8;
-          const uint64_t gj = j0 + jg;
-          uint2 bytes[4] = {};
-          const bool live = gk < k && gj < n;
-          switch (L) {
+        const int kk = threadIdx.x / 4, jg = 8 * (threadIdx.x % 4);
+        const uint64_t gk = k0 + kk, gj = j0 + jg;
+        uint2 bytes[4] = {};
+        const bool live = gk < k && gj < n;
+        switch (L) {
 #define CCM_TC_NIB(LL)                                                           \
   case LL:                                                                       \
     if (live) {                                                                  \
@@ -252,44 +241,37 @@ __global__ void __launch_bounds__(256) k_limbs_bt(const ccm_header* out, const c
           plane_bytes8<LL>(wg, l, sgn && l == LL - 1);                           \
     }                                                                            \
     break;
-            CCM_TC_NIB(1) CCM_TC_NIB(2) CCM_TC_NIB(3) CCM_TC_NIB(4)
+          CCM_TC_NIB(1) CCM_TC_NIB(2) CCM_TC_NIB(3) CCM_TC_NIB(4)
 #undef CCM_TC_NIB
-            default: break;
-          }
-          for (int l = 0; l < L; ++l) {
+          default: break;
+        }
+        for (int l = 0; l < L; ++l) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-              tile[l][jg + q][kk] = (uint8_t)((q < 4 ? bytes[l].x : bytes[l].y) >> (8 * (q & 3)));
-          }
+          for (int q = 0; q < 8; ++q)
+            tile[l][jg + q][kk] = (uint8_t)((q < 4 ? bytes[l].x : bytes[l].y) >> (8 * (q & 3)));
         }
       } else {
-        // read: thread covers (kk = threadIdx.x / 32 + 8 r, j = threadIdx.x % 32 + 32 q)
+        // read: thread covers (kk = threadIdx.x / 32 + 8 r, j = threadIdx.x % 32)
         for (int r = 0; r < 8; ++r) {
-          for (int q = 0; q < kBtN / 32; ++q) {
-            const int kk = threadIdx.x / 32 + 8 * r, j = threadIdx.x % 32 + 32 * q;
-            const uint64_t gk = k0 + kk, gj = j0 + j;
-            const int64_t v = (gk < k && gj < n) ? decode_field(w, gk * n + gj, b, sgn) : 0;
-            for (int l = l0; l < L && l < l0 + 4; ++l)
-              tile[l - l0][j][kk] = e4m3_of_digit(digit(v, l, L));
-          }
+          const int kk = threadIdx.x / 32 + 8 * r, j = threadIdx.x % 32;
+          const uint64_t gk = k0 + kk, gj = j0 + j;
+          const int64_t v = (gk < k && gj < n) ? decode_field(w, gk * n + gj, b, sgn) : 0;
+          for (int l = l0; l < L && l < l0 + 4; ++l)
+            tile[l - l0][j][kk] = e4m3_of_digit(digit(v, l, L));
         }
       }
       __syncthreads();
-      // write: 128 rows (j) x 64 bytes per digit plane, 16 bytes per store
+      // write: 32 rows (j) x 64 bytes per digit plane, 16 bytes per thread
       for (int l = l0; l < L && l < l0 + 4; ++l) {
-#pragma unroll
-        for (int rep = 0; rep < kBtN * (kBtK / 16) / 256; ++rep) {
-          const int idx = threadIdx.x + 256 * rep;
-          const int j = idx / 4, part = idx % 4;
-          if (j0 + j < n_pad) {
-            const uint8_t* src = &tile[l - l0][j][16 * part];
-            uint4 v;
-            v.x = src[0] | src[1] << 8 | src[2] << 16 | (uint32_t)src[3] << 24;
-            v.y = src[4] | src[5] << 8 | src[6] << 16 | (uint32_t)src[7] << 24;
-            v.z = src[8] | src[9] << 8 | src[10] << 16 | (uint32_t)src[11] << 24;
-            v.w = src[12] | src[13] << 8 | src[14] << 16 | (uint32_t)src[15] << 24;
-            *reinterpret_cast<uint4*>(planes + l * plane + (j0 + j) * k_pad + k0 + 16 * part) = v;
-          }
+        const int j = threadIdx.x / 4, part = threadIdx.x % 4;
+        if (threadIdx.x < 128) {
+          const uint8_t* src = &tile[l - l0][j][16 * part];
+          uint4 v;
+          v.x = src[0] | src[1] << 8 | src[2] << 16 | (uint32_t)src[3] << 24;
+          v.y = src[4] | src[5] << 8 | src[6] << 16 | (uint32_t)src[7] << 24;
+          v.z = src[8] | src[9] << 8 | src[10] << 16 | (uint32_t)src[11] << 24;
+          v.w = src[12] | src[13] << 8 | src[14] << 16 | (uint32_t)src[15] << 24;
+          *reinterpret_cast<uint4*>(planes + l * plane + (j0 + j) * k_pad + k0 + 16 * part) = v;
         }
       }
       __syncthreads();
@@ -680,8 +662,8 @@ int run_matmul_tc(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c,
     const uint64_t quads = p.m_pad * p.k_pad / 4;
     int g = (int)umin((quads + 255) / 256, (uint64_t)num_sms() * 16);
     tc::k_limbs_a<<<g, 256, 0, st>>>(c.hdr, a.hdr, a.words, m, k, p.m_pad, p.k_pad, L, pa);
-    const uint64_t tiles = (p.k_pad / tc::kBtK) * ((p.n_pad + tc::kBtN - 1) / tc::kBtN);
-    int g2 = (int)umin(tiles, (uint64_t)num_sms() * 8);
+    const uint64_t tiles = (p.k_pad / 64) * (p.n_pad / 32);
+    int g2 = (int)umin(tiles, (uint64_t)num_sms() * 16);
     tc::k_limbs_bt<<<g2, 256, 0, st>>>(c.hdr, b.hdr, b.words, k, n, p.n_pad, p.k_pad, L, pb);
     note_launch(2);
   }
