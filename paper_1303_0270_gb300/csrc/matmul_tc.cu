@@ -45,6 +45,7 @@ constexpr int kBM = 128;    // rows of A / C per tile (UMMA M)
 constexpr int kBK = 128;    // K elements (= bytes of e4m3) per pipeline stage
 constexpr int kThreads = 128;
 constexpr uint32_t kSpinLimit = 1u << 26;  // bounded mbarrier waits
+constexpr uint32_t kGroupM = 8;            // tile rows per raster group
 
 // Tile geometry for L digits per operand.
 struct Geo {
@@ -416,8 +417,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) skip_s = args.out->status != CCM_OK;
   __syncthreads();
   if (skip_s) return;
+  // Grouped raster: consecutive CTAs sweep the tile columns of a group of
+  // kGroupM tile rows before the next group, so a wave of CTAs reads a
+  // handful of A and B tile rows many times from L2 instead of all of B.
   const uint32_t tile = blockIdx.x;
-  const uint32_t tm = tile / args.tiles_n, tn = tile % args.tiles_n;
+  const uint32_t tiles_m = gridDim.x / args.tiles_n;
+  const uint32_t per_group = kGroupM * args.tiles_n, group = tile / per_group;
+  const uint32_t first_m = group * kGroupM;
+  const uint32_t gm = tiles_m - first_m < kGroupM ? tiles_m - first_m : kGroupM;
+  const uint32_t in_group = tile - group * per_group;
+  const uint32_t tm = first_m + in_group % gm, tn = in_group / gm;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
