@@ -43,7 +43,6 @@ namespace tc {
 
 constexpr int kBM = 128;    // rows of A / C per tile (UMMA M)
 constexpr int kBK = 128;    // K elements (= bytes of e4m3) per pipeline stage
-constexpr int kThreads = 128;
 constexpr uint32_t kSpinLimit = 1u << 26;  // bounded mbarrier waits
 constexpr uint32_t kGroupM = 8;            // tile rows per raster group
 
@@ -53,6 +52,8 @@ struct Geo {
   int classes = 0;  // 2L - 1 accumulators
   int bn = 0;       // UMMA N
   int stages = 0;
+  int accs = 0;     // accumulator sets in tensor memory (2: a tile's epilogue
+                    // overlaps the next tile's MMAs)
   int tmem_cols = 0;
 };
 
@@ -64,9 +65,10 @@ __host__ __device__ constexpr Geo geometry(int L) {
   const int stage_bytes = L * kBK * (kBM + g.bn);
   g.stages = 200 * 1024 / stage_bytes;
   if (g.stages > 4) g.stages = 4;
-  int cols = g.classes * g.bn;
+  const int cols = g.classes * g.bn;
+  g.accs = 2 * cols <= 512 ? 2 : 1;
   int p = 32;
-  while (p < cols) p <<= 1;
+  while (p < g.accs * cols) p <<= 1;
   g.tmem_cols = p;
   return g;
 }
@@ -392,53 +394,75 @@ struct MmArgs {
   uint32_t a_rows_pad;  // rows per A digit plane (m_pad)
   uint32_t b_rows_pad;  // rows per B digit plane (n_pad)
   uint32_t tiles_n;     // n_pad / bn
+  uint32_t tiles_m;     // m_pad / kBM
   int L;
   int c32;              // 1: C is written as int32 (the output capacity bounds its width by 31)
 };
 
+// Output tile t (grouped raster): consecutive tiles sweep the tile columns
+// of a group of kGroupM tile rows before the next group.
+__device__ __forceinline__ void tile_coords(uint32_t t, uint32_t tiles_m, uint32_t tiles_n,
+                                            uint32_t& tm, uint32_t& tn) {
+  const uint32_t per_group = kGroupM * tiles_n, group = t / per_group;
+  const uint32_t first_m = group * kGroupM;
+  const uint32_t gm = tiles_m - first_m < kGroupM ? tiles_m - first_m : kGroupM;
+  const uint32_t in_group = t - group * per_group;
+  tm = first_m + in_group % gm;
+  tn = in_group / gm;
+}
+
+// Persistent, warp-specialised: one CTA per SM walks the output tiles t =
+// blockIdx.x, + gridDim.x, ...  Warp 0 (one thread) streams the digit-plane
+// tiles of every k block of every tile through the S-stage ring (TMA,
+// mbarriers); warp 1 allocates tensor memory and one of its threads issues
+// the MMAs of tile i into accumulator set i % accs, once the epilogue has
+// emptied that set; warps 2-5 (tensor-memory lane quadrants 2, 3, 0, 1) read
+// the classes of each finished tile, combine them exactly and store C.  The
+// producer runs on into the next tile's loads while the current one is
+// finished, and with two accumulator sets (one digit) the next tile's MMAs
+// run during the previous tile's epilogue.
+constexpr int kThreadsP = 192;
+
 template <int L>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreadsP, 1)
     k_mm_tc(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
             MmArgs args) {
   constexpr Geo G = geometry(L);
-  constexpr int BN = G.bn, S = G.stages, C = G.classes;
+  constexpr int BN = G.bn, S = G.stages, C = G.classes, NACC = G.accs;
+  constexpr uint32_t ACC_COLS = (uint32_t)(C * BN);          // columns of one accumulator set
   constexpr uint32_t A_TILE = kBM * kBK, B_TILE = BN * kBK;  // bytes per digit plane tile
   constexpr uint32_t STAGE = L * (A_TILE + B_TILE);
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~(uintptr_t)1023);
-  __shared__ uint64_t full_bar[S], empty_bar[S], accum_bar;
+  __shared__ uint64_t full_bar[S], empty_bar[S], acc_full[NACC], acc_empty[NACC];
   __shared__ uint32_t tmem_base_s;
-  __shared__ int abort_s, skip_s;
-  __shared__ uint32_t issued_s;  // k blocks whose loads the producer issued
+  __shared__ int skip_s;
+  __shared__ volatile int abort_s;
+  __shared__ uint32_t issued_s;  // k blocks whose loads the producer issued (all tiles)
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   // one read of the status for the whole CTA (another CTA may change it)
   if (threadIdx.x == 0) skip_s = args.out->status != CCM_OK;
   __syncthreads();
   if (skip_s) return;
-  // Grouped raster: consecutive CTAs sweep the tile columns of a group of
-  // kGroupM tile rows before the next group, so a wave of CTAs reads a
-  // handful of A and B tile rows many times from L2 instead of all of B.
-  const uint32_t tile = blockIdx.x;
-  const uint32_t tiles_m = gridDim.x / args.tiles_n;
-  const uint32_t per_group = kGroupM * args.tiles_n, group = tile / per_group;
-  const uint32_t first_m = group * kGroupM;
-  const uint32_t gm = tiles_m - first_m < kGroupM ? tiles_m - first_m : kGroupM;
-  const uint32_t in_group = tile - group * per_group;
-  const uint32_t tm = first_m + in_group % gm, tn = in_group / gm;
+  const uint32_t tiles = args.tiles_m * args.tiles_n;
+  const uint32_t nk = args.k_blocks;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    mbar_init(&accum_bar, 1);
+    for (int a = 0; a < NACC; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 4);  // one arrival per epilogue warp
+    }
     abort_s = 0;
     issued_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                      smem_u32(&tmem_base_s)),
                  "r"((uint32_t)G.tmem_cols));
@@ -448,120 +472,156 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = tmem_base_s;
-  const uint32_t nk = args.k_blocks;
 
-  if (warp == 0 && lane == 0) {
-    // TMA producer
-    for (uint32_t kb = 0; kb < nk; ++kb) {
-      const int s = kb % S;
-      if (kb >= (uint32_t)S && !mbar_wait(&empty_bar[s], ((kb / S) - 1) & 1)) {
+  uint64_t orv = 0;
+  uint32_t neg = 0;
+  if (warp == 0) {
+    if (lane == 0) {
+      // TMA producer over every k block of every tile of this CTA
+      uint32_t g = 0;
+      for (uint32_t t = blockIdx.x; t < tiles && !abort_s; t += gridDim.x) {
+        uint32_t tm, tn;
+        tile_coords(t, args.tiles_m, args.tiles_n, tm, tn);
+        for (uint32_t kb = 0; kb < nk; ++kb, ++g) {
+          const int s = g % S;
+          if (g >= (uint32_t)S && !mbar_wait(&empty_bar[s], ((g / S) - 1) & 1)) {
+            abort_s = 1;
+            break;
+          }
+          if (abort_s) break;
+          uint8_t* st = smem + s * STAGE;
+          mbar_expect_tx(&full_bar[s], STAGE);
+          for (int l = 0; l < L; ++l) {
+            tma_load_2d(st + l * A_TILE, &tm_a, &full_bar[s], kb * kBK,
+                        l * args.a_rows_pad + tm * kBM);
+            tma_load_2d(st + L * A_TILE + l * B_TILE, &tm_b, &full_bar[s], kb * kBK,
+                        l * args.b_rows_pad + tn * BN);
+          }
+          issued_s = g + 1;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer
+      constexpr uint32_t idesc = idesc_e4m3_f32(kBM, BN);
+      uint32_t g = 0, i = 0;
+      bool ok = true;
+      for (uint32_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++i) {
+        const uint32_t a = i % NACC;
+        if (i >= (uint32_t)NACC && !mbar_wait(&acc_empty[a], ((i / NACC) - 1) & 1)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t acc0 = tmem + a * ACC_COLS;
+        uint32_t started = 0;  // classes already holding a partial sum
+        for (uint32_t kb = 0; kb < nk; ++kb, ++g) {
+          const int s = g % S;
+          if (abort_s || !mbar_wait(&full_bar[s], (g / S) & 1)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const uint32_t st = smem_u32(smem + s * STAGE);
+#pragma unroll
+          for (int l = 0; l < L; ++l) {
+#pragma unroll
+            for (int mm = 0; mm < L; ++mm) {
+              const int c = l + mm;
+              const uint32_t a0 = st + l * A_TILE, b0 = st + L * A_TILE + mm * B_TILE;
+#pragma unroll
+              for (int kk = 0; kk < kBK / 32; ++kk) {
+                const uint32_t acc = ((started >> c) & 1u) | (kk > 0 ? 1u : 0u);
+                mma_e4m3(acc0 + c * BN, smem_desc_sw128(a0 + 32 * kk),
+                         smem_desc_sw128(b0 + 32 * kk), idesc, acc);
+              }
+              started |= 1u << c;
+            }
+          }
+          mma_commit(&empty_bar[s]);  // frees the stage once these MMAs have read it
+        }
+        mma_commit(&acc_full[a]);  // (also when giving up: the MMAs issued so far complete)
+      }
+      if (!ok) abort_s = 1;
+    }
+  } else {
+    // epilogue: tensor-memory lane quadrant q of every finished tile
+    const int q = warp % 4;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    uint32_t i = 0;
+    for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+      const uint32_t a = i % NACC;
+      // (one decision for the whole warp: the tensor-memory loads are warp-wide)
+      if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[a], (i / NACC) & 1))) {
         abort_s = 1;
         break;
       }
-      uint8_t* st = smem + s * STAGE;
-      mbar_expect_tx(&full_bar[s], STAGE);
-      for (int l = 0; l < L; ++l) {
-        tma_load_2d(st + l * A_TILE, &tm_a, &full_bar[s], kb * kBK,
-                    l * args.a_rows_pad + tm * kBM);
-        tma_load_2d(st + L * A_TILE + l * B_TILE, &tm_b, &full_bar[s], kb * kBK,
-                    l * args.b_rows_pad + tn * BN);
-      }
-      issued_s = kb + 1;
-    }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    constexpr uint32_t idesc = idesc_e4m3_f32(kBM, BN);
-    uint32_t started = 0;  // classes already holding a partial sum
-    bool ok = true;
-    for (uint32_t kb = 0; kb < nk; ++kb) {
-      const int s = kb % S;
-      if (!mbar_wait(&full_bar[s], (kb / S) & 1)) {
-        ok = false;
-        break;
-      }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint32_t st = smem_u32(smem + s * STAGE);
+      if (__any_sync(0xffffffffu, abort_s != 0)) break;
+      uint32_t tm, tn;
+      tile_coords(t, args.tiles_m, args.tiles_n, tm, tn);
+      const uint64_t row = (uint64_t)tm * kBM + q * 32 + lane;
+      const uint32_t acc0 = tmem + lane_base + a * ACC_COLS;
+#pragma unroll 1
+      for (int col0 = 0; col0 < BN; col0 += 32) {
+        int64_t acc[32];
 #pragma unroll
-      for (int l = 0; l < L; ++l) {
+        for (int j = 0; j < 32; ++j) acc[j] = 0;
+#pragma unroll 1
+        for (int c = 0; c < C; ++c) {
+          uint32_t r[32];
+          tmem_ld32(acc0 + c * BN + col0, r);
 #pragma unroll
-        for (int mm = 0; mm < L; ++mm) {
-          const int c = l + mm;
-          const uint32_t a0 = st + l * A_TILE, b0 = st + L * A_TILE + mm * B_TILE;
+          for (int j = 0; j < 32; ++j)
+            acc[j] += (int64_t)__float2ll_rn(__uint_as_float(r[j])) * (int64_t)(1ll << (4 * c));
+        }
+        const uint64_t col = (uint64_t)tn * BN + col0;
+        if (row < args.m) {
+          int64_t* dst = args.c + row * args.n + col;
+          int32_t* dst32 = reinterpret_cast<int32_t*>(args.c) + row * args.n + col;
 #pragma unroll
-          for (int kk = 0; kk < kBK / 32; ++kk) {
-            const uint32_t acc = ((started >> c) & 1u) | (kk > 0 ? 1u : 0u);
-            mma_e4m3(tmem + c * BN, smem_desc_sw128(a0 + 32 * kk), smem_desc_sw128(b0 + 32 * kk),
-                     idesc, acc);
+          for (int j = 0; j < 32; ++j) {
+            if (col + j < args.n) {
+              if (args.c32)
+                dst32[j] = (int32_t)acc[j];  // (statistics from the exact value below)
+              else
+                dst[j] = acc[j];
+              orv |= fold(acc[j]);
+              neg |= (uint32_t)(acc[j] < 0);
+            }
           }
-          started |= 1u << c;
         }
       }
-      mma_commit(&empty_bar[s]);  // frees the stage once these MMAs have read it
+      // this set's tensor memory has been read: the MMAs of tile i + accs may start
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&acc_empty[a]))
+                     : "memory");
     }
-    if (!ok) abort_s = 1;
-    mma_commit(&accum_bar);
+    orv = warp_or64(orv);
+    neg = __reduce_or_sync(0xffffffffu, neg);
+    if (lane == 0) {
+      if (orv) atomicOr(reinterpret_cast<unsigned long long*>(&args.out->stat_or),
+                        (unsigned long long)orv);
+      if (neg) atomicOr(&args.out->stat_neg, 1u);
+    }
   }
   __syncwarp();
-
-  // Epilogue: wait for the accumulators, combine the classes exactly.
-  const bool have = mbar_wait(&accum_bar, 0);
-  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  __syncthreads();
-  const bool failed = !have || abort_s;
-  if (failed && threadIdx.x == 0) {
-    // a wait gave up: let the copies already issued land (bounded) before the
-    // CTA's shared memory is released
-    const uint32_t issued = issued_s;
-    for (uint32_t kb = issued > (uint32_t)S ? issued - S : 0; kb < issued; ++kb)
-      mbar_wait(&full_bar[kb % S], (kb / S) & 1);
-  }
-  uint64_t orv = 0;
-  uint32_t neg = 0;
-  if (!failed) {
-    const uint64_t row = (uint64_t)tm * kBM + warp * 32 + lane;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-#pragma unroll 1
-    for (int col0 = 0; col0 < BN; col0 += 32) {
-      int64_t acc[32];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) acc[j] = 0;
-#pragma unroll 1
-      for (int c = 0; c < C; ++c) {
-        uint32_t r[32];
-        tmem_ld32(tmem + lane_base + c * BN + col0, r);
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          acc[j] += (int64_t)__float2ll_rn(__uint_as_float(r[j])) * (int64_t)(1ll << (4 * c));
-      }
-      const uint64_t col = (uint64_t)tn * BN + col0;
-      if (row < args.m) {
-        int64_t* dst = args.c + row * args.n + col;
-        int32_t* dst32 = reinterpret_cast<int32_t*>(args.c) + row * args.n + col;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          if (col + j < args.n) {
-            if (args.c32)
-              dst32[j] = (int32_t)acc[j];  // (statistics from the exact value below)
-            else
-              dst[j] = acc[j];
-            orv |= fold(acc[j]);
-            neg |= (uint32_t)(acc[j] < 0);
-          }
-        }
-      }
-    }
-  }
-  orv = warp_or64(orv);
-  neg = __reduce_or_sync(0xffffffffu, neg);
-  if (lane == 0) {
-    if (orv) atomicOr(reinterpret_cast<unsigned long long*>(&args.out->stat_or),
-                      (unsigned long long)orv);
-    if (neg) atomicOr(&args.out->stat_neg, 1u);
-  }
-  if (failed && threadIdx.x == 0) set_status(args.out, CCM_E_TIMEOUT);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
-  if (warp == 0) {
+  if (abort_s && threadIdx.x == 0) {
+    // a wait gave up: let the copies already issued land (bounded) before the
+    // CTA's shared memory is released, and report it
+    const uint32_t issued = issued_s;
+    for (uint32_t g = issued > (uint32_t)S ? issued - S : 0; g < issued; ++g)
+      mbar_wait(&full_bar[g % S], (g / S) & 1);
+    set_status(args.out, CCM_E_TIMEOUT);
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
                  "r"((uint32_t)G.tmem_cols));
   }
@@ -656,7 +716,7 @@ static void launch_mm(const CUtensorMap& ta, const CUtensorMap& tb, const tc::Mm
     cudaFuncSetAttribute(tc::k_mm_tc<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  tc::k_mm_tc<L><<<grid, tc::kThreads, smem, st>>>(ta, tb, args);
+  tc::k_mm_tc<L><<<grid, tc::kThreadsP, smem, st>>>(ta, tb, args);
 }
 
 int run_matmul_tc(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c,
@@ -682,9 +742,12 @@ int run_matmul_tc(const ccm_matrix& a, const ccm_matrix& b, const ccm_matrix& c,
       !tc::make_map(&tb, pb, p.k_pad, (uint64_t)L * p.n_pad, (uint32_t)g.bn))
     return CCM_E_CUDA;
   tc::MmArgs args{c.hdr, c_scratch, m, n, (uint32_t)(p.k_pad / tc::kBK), (uint32_t)p.m_pad,
-                  (uint32_t)p.n_pad, (uint32_t)(p.n_pad / g.bn), L,
-                  matmul_c32(c) ? 1 : 0};
-  const unsigned grid = (unsigned)((p.m_pad / tc::kBM) * (p.n_pad / g.bn));
+                  (uint32_t)p.n_pad, (uint32_t)(p.n_pad / g.bn), (uint32_t)(p.m_pad / tc::kBM),
+                  L, matmul_c32(c) ? 1 : 0};
+  // persistent: one CTA per SM (the stages fill its shared memory), or one
+  // per tile when there are fewer tiles
+  const uint64_t tiles = (p.m_pad / tc::kBM) * (p.n_pad / g.bn);
+  const unsigned grid = (unsigned)umin(tiles, (uint64_t)num_sms());
   profile_begin(st);
   switch (L) {
     case 1: launch_mm<1>(ta, tb, args, grid, st); break;
