@@ -893,23 +893,29 @@ __global__ void __launch_bounds__(kThreads) k_pack_local(const T* __restrict__ s
   // dynamic: kWarps x 2 buffers x kStageWords uint32 words
   constexpr int kStageWords = sizeof(T) == 8 ? 2 * kDensePad : kDensePad32;
   extern __shared__ __align__(16) uint32_t s_dyn[];
-  if (out->status != CCM_OK) return;
-  // b_spec < 0: the statistics are already in the header (an epilogue merged
-  // them): the width is exact and every tile goes straight to its place
-  const bool exact = b_spec < 0;
-  if (exact) b_spec = width_from_stats(out->stat_or, out->stat_neg);
   const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
   uint32_t* buf0 = s_dyn + warp * 2 * kStageWords;
   const uint64_t ntiles = (n + kTile - 1) / kTile;
   const uint64_t gwarps = (uint64_t)gridDim.x * kWarps;
-  uint64_t g_or = 0;
-  uint32_t g_neg = 0;
   uint64_t tile = (uint64_t)blockIdx.x * kWarps + warp;
-  int cur = 0;
+  // the first dense tile is requested before the header is looked at: with
+  // a programmatic launch this overlaps the header's initialisation
   if (tile < ntiles)
     issue_dense_tile(reinterpret_cast<T*>(buf0), src, tile * kTile,
                      (uint32_t)umin((uint64_t)kTile, n - tile * kTile), lane);
   cp_async_commit_ge();
+  ax::grid_dep_wait();
+  if (out->status != CCM_OK) {
+    cp_async_wait0_ge();
+    return;
+  }
+  // b_spec < 0: the statistics are already in the header (an epilogue merged
+  // them): the width is exact and every tile goes straight to its place
+  const bool exact = b_spec < 0;
+  if (exact) b_spec = width_from_stats(out->stat_or, out->stat_neg);
+  uint64_t g_or = 0;
+  uint32_t g_neg = 0;
+  int cur = 0;
   // the speculation flag as this warp last saw it (sticky once set, so a
   // warp stops reading it after the first time it finds it set)
   bool known = exact;
@@ -1167,6 +1173,7 @@ struct EwCall {
   int slot_class;         // Local* / Repack: width class of the output (slot = 32*class words)
   int spec;               // AddPack / ScalePack: an AddSpec / ScaleSpec launch came first;
                           // LocalI64 / LocalI32 / Repack: the speculative width (0: none)
+  int pdl;                // LocalI64 / LocalI32: launched with programmatic dependent launch
 };
 
 inline int ew_grid(uint64_t n, int per_sm) {
@@ -1261,14 +1268,24 @@ int launch_ew_pack(const EwCall& c, cudaStream_t st) {
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
           attr = true;
         }
-        k_pack_local<int64_t, C><<<gl, kThreads, smem, st>>>((const int64_t*)c.dense, c.out,
-                                                             slots, slot_words, widths, n,
-                                                             c.words, c.spec);
+        if (c.pdl)
+          ax::launch_pdl(k_pack_local<int64_t, C>, dim3(gl), dim3(kThreads), smem, st,
+                         (const int64_t*)c.dense, c.out, slots, slot_words, widths, n, c.words,
+                         c.spec);
+        else
+          k_pack_local<int64_t, C><<<gl, kThreads, smem, st>>>((const int64_t*)c.dense, c.out,
+                                                               slots, slot_words, widths, n,
+                                                               c.words, c.spec);
       } else if (c.kind == EwKind::LocalI32) {
         const size_t smem = (size_t)kWarps * 2 * kDensePad32 * sizeof(uint32_t);
-        k_pack_local<int32_t, C><<<gl, kThreads, smem, st>>>((const int32_t*)c.dense, c.out,
-                                                             slots, slot_words, widths, n,
-                                                             c.words, c.spec);
+        if (c.pdl)
+          ax::launch_pdl(k_pack_local<int32_t, C>, dim3(gl), dim3(kThreads), smem, st,
+                         (const int32_t*)c.dense, c.out, slots, slot_words, widths, n, c.words,
+                         c.spec);
+        else
+          k_pack_local<int32_t, C><<<gl, kThreads, smem, st>>>((const int32_t*)c.dense, c.out,
+                                                               slots, slot_words, widths, n,
+                                                               c.words, c.spec);
       } else {
         ax::launch_pdl(k_repack<C>, dim3(gl), dim3(kThreads), 0, st, (const uint32_t*)slots,
                        slot_words, (const uint8_t*)widths, c.out, c.words, c.capacity, n,

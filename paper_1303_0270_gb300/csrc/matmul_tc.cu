@@ -372,6 +372,24 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       : "memory");
 }
 
+// tcgen05.ld of 32 columns without the wait (several in flight, then
+// tmem_ld_wait before the registers are used).
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -568,13 +586,34 @@ __global__ void __launch_bounds__(kThreadsP, 1)
         int64_t acc[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) acc[j] = 0;
+        if constexpr (C <= 3) {
+          // two classes' loads in flight at a time (for more classes the
+          // registers this takes cost more than the overlap gains)
 #pragma unroll 1
-        for (int c = 0; c < C; ++c) {
-          uint32_t r[32];
-          tmem_ld32(acc0 + c * BN + col0, r);
+          for (int c = 0; c < C; c += 2) {
+            uint32_t r0[32], r1[32];
+            tmem_ld32_async(acc0 + c * BN + col0, r0);
+            if (c + 1 < C) tmem_ld32_async(acc0 + (c + 1) * BN + col0, r1);
+            tmem_ld_wait();
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            acc[j] += (int64_t)__float2ll_rn(__uint_as_float(r[j])) * (int64_t)(1ll << (4 * c));
+            for (int j = 0; j < 32; ++j)
+              acc[j] += (int64_t)__float2ll_rn(__uint_as_float(r0[j])) * (int64_t)(1ll << (4 * c));
+            if (c + 1 < C) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                acc[j] += (int64_t)__float2ll_rn(__uint_as_float(r1[j])) *
+                          (int64_t)(1ll << (4 * (c + 1)));
+            }
+          }
+        } else {
+#pragma unroll 1
+          for (int c = 0; c < C; ++c) {
+            uint32_t r[32];
+            tmem_ld32(acc0 + c * BN + col0, r);
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              acc[j] += (int64_t)__float2ll_rn(__uint_as_float(r[j])) * (int64_t)(1ll << (4 * c));
+          }
         }
         const uint64_t col = (uint64_t)tn * BN + col0;
         if (row < args.m) {

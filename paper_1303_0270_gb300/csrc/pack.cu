@@ -3,6 +3,7 @@
 // access, and the elementwise operations whose results are re-packed by the
 // same engine (add, scale).
 #include "ew_kernels.cuh"
+#include "async_copy.cuh"
 #include "kernels.h"
 #include "pack_engine.cuh"
 
@@ -62,6 +63,7 @@ int max_smem_optin() {
 }
 
 __global__ void k_init(InitArgs a) {
+  ax::grid_dep_launch();  // a programmatically launched successor may start now
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     int st = CCM_OK;
     if (a.in0) st = check_input(a.in0, a.in0_rows, a.in0_cols, a.in0_capacity);
@@ -186,6 +188,8 @@ void run_pack(const void* dense, int dtype, uint64_t rows, uint64_t cols, const 
     // the widest width the output's capacity holds: the speculative width
     c.spec = width_bound(out.capacity, n);
     if (c.spec > cls) c.spec = 0;
+    // (starts while the header is initialised, unless this call is timed)
+    c.pdl = profile_armed() ? 0 : 1;
     profile_begin(st);
     launch_ew(cls, c, st);
     profile_end(st);
