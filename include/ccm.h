@@ -357,7 +357,11 @@ ccm_status ccm_batch_matvec(const void* plan, const ccm_batch_info* info, void* 
  * cols, 0) bytes, 256-byte aligned.  A stream needing more than `capacity`
  * words: CCM_E_CAPACITY in the header.
  * ccm_vlb_unpack: entries back to `dense` (`dtype`); CCM_I32 needs L <= 31.
- * Status to `*err` (device, may be NULL) as for ccm_unpack. */
+ * Status to `*err` (device, may be NULL) as for ccm_unpack; a stream that does
+ * not parse (a length outside [1, largest L], or an index chunk that does not
+ * end where the next index entry says) sets CCM_E_INPUT.  `words` 16-byte
+ * aligned takes the fast decoder (a register bit window per lane, the stream
+ * staged by cp.async); any 4-byte alignment is accepted. */
 #define CCM_VLB_MAGIC 0x31564343u /* "CCV1" */
 #define CCM_VLB_INDEX_STRIDE 64
 uint64_t ccm_vlb_index_entries(uint64_t rows, uint64_t cols);
