@@ -75,10 +75,14 @@ struct PackedIn {
       t.r[j] = v;
     }
   }
-  // Global -> shared in plain word order with 16-byte cp.async (zero past
-  // the data words), for the lane pass at compile-time width B (= b).
+  // Global -> shared in plain word order for the lane pass at compile-time
+  // width B (= b): the data words of tile `tile`, rounded up to 16 bytes
+  // (the canonical zero padding of the stream), by one bulk copy that lane 0
+  // issues on `bar`; the warp zeroes the rest of the buffer first.  Returns
+  // the bytes the copy brings (all lanes).
   template <int B>
-  __device__ __forceinline__ void issue_tile(uint64_t tile, uint32_t* buf, int lane) const;
+  __device__ __forceinline__ uint32_t fill_tile(uint64_t tile, uint32_t* buf, uint64_t* bar,
+                                                int lane) const;
   // Registers -> shared staging layout.
   template <int BMAX>
   __device__ __forceinline__ void stage(const TileRegs<BMAX>& t, uint32_t* buf, int lane) const {
@@ -132,18 +136,16 @@ __device__ __forceinline__ void cp_async_wait2_ge() {
 }
 
 template <int B>
-__device__ __forceinline__ void PackedIn::issue_tile(uint64_t tile, uint32_t* buf,
-                                                    int lane) const {
-  const uint64_t w0 = tile * (uint64_t)(32 * B);
-#pragma unroll
-  for (int j = 0; j < (8 * B + 31) / 32; ++j) {
-    const int q = lane + 32 * j;
-    if (q < 8 * B) {
-      const uint64_t g = w0 + 4 * (uint64_t)q;
-      const uint32_t bytes = g + 4 <= dw ? 16u : (g < dw ? (uint32_t)(dw - g) * 4u : 0u);
-      cp_async16_zfill(buf + 4 * q, w + (bytes ? g : 0), bytes);
-    }
-  }
+__device__ __forceinline__ uint32_t PackedIn::fill_tile(uint64_t tile, uint32_t* buf,
+                                                       uint64_t* bar, int lane) const {
+  constexpr uint32_t TW = 32 * B;
+  const uint64_t w0 = tile * (uint64_t)TW;
+  const uint32_t valid = (uint32_t)umin((uint64_t)TW, dw - w0);  // tile < ntiles: w0 < dw
+  const uint32_t cw = (valid + 3u) & ~3u;
+  if (cw < TW)  // the last tile: zero words past the copy (fields past n read 0)
+    for (uint32_t i = cw + lane; i < TW; i += 32) buf[i] = 0;
+  if (lane == 0) ax::bulk_g2s(buf, w + w0, 4 * cw, bar);
+  return 4 * cw;
 }
 
 // Byte lanes: four fields of at most 8 bits in one 32-bit register, field k
@@ -296,6 +298,13 @@ __device__ __forceinline__ uint64_t offset_out64(uint64_t r, uint64_t& orb, uint
   return r ^ top;
 }
 
+// Bytes fill_tile brings for tile `tile` of input x at width B.
+template <int B>
+__device__ __forceinline__ uint32_t lanes_fill_bytes(const PackedIn& x, uint64_t tile) {
+  const uint64_t w0 = tile * (uint64_t)(32 * B);
+  return 4 * (((uint32_t)umin((uint64_t)(32 * B), x.dw - w0) + 3u) & ~3u);
+}
+
 struct OpAdd {
   PackedIn a, b;
   template <int BMAX>
@@ -358,11 +367,14 @@ struct OpAdd {
   }
   static constexpr bool kTwoInputs = true;
   // cp.async of tile `tile` of both inputs into plain-order shared buffers
+  // tile `tile` of both inputs into plain-order shared buffers, one bulk
+  // copy each on `bar` (lane 0 arms it with the bytes of both)
   template <int B>
-  __device__ __forceinline__ void lanes_issue(uint64_t tile, uint32_t* bufa, uint32_t* bufb,
-                                              int lane) const {
-    a.template issue_tile<B>(tile, bufa, lane);
-    b.template issue_tile<B>(tile, bufb, lane);
+  __device__ __forceinline__ void lanes_fill(uint64_t tile, uint32_t* bufa, uint32_t* bufb,
+                                             uint64_t* bar, int lane) const {
+    if (lane == 0) ax::mbar_expect_tx(bar, 2 * lanes_fill_bytes<B>(a, tile));
+    a.template fill_tile<B>(tile, bufa, bar, lane);
+    b.template fill_tile<B>(tile, bufb, bar, lane);
   }
   template <int BMAX>
   __device__ __forceinline__ void prefetch(Regs<BMAX>& r, uint64_t tile, int lane) const {
@@ -486,9 +498,10 @@ struct OpScale {
   }
   static constexpr bool kTwoInputs = false;
   template <int B>
-  __device__ __forceinline__ void lanes_issue(uint64_t tile, uint32_t* bufa, uint32_t*,
-                                              int lane) const {
-    a.template issue_tile<B>(tile, bufa, lane);
+  __device__ __forceinline__ void lanes_fill(uint64_t tile, uint32_t* bufa, uint32_t*,
+                                             uint64_t* bar, int lane) const {
+    if (lane == 0) ax::mbar_expect_tx(bar, lanes_fill_bytes<B>(a, tile));
+    a.template fill_tile<B>(tile, bufa, bar, lane);
   }
   template <int BMAX>
   __device__ __forceinline__ void prefetch(Regs<BMAX>& r, uint64_t tile, int lane) const {
@@ -524,8 +537,9 @@ constexpr int kStats = 0, kPack = 1, kSpec = 2;
 // general kSpec launch returns at once; otherwise it returns and the general
 // pass runs.  Input width B, output width BS, lane size L (8, 16 or 32 bits:
 // four, two or one field per register) and sign mode are compile-time.
-// Per tile the inputs are staged in plain word order through a cp.async
-// ring; each lane reads its group's B words with the widest aligned vector
+// Per tile the inputs are staged in plain word order through a ring of
+// bulk copies (one per input tile, issued by lane 0 on the slot's mbarrier,
+// waits bounded); each lane reads its group's B words with the widest aligned vector
 // (signed inputs: XOR of the sign bits), forms the results a register of
 // lanes at a time (one add or multiply for 4, 2 or 1 fields), ORs the
 // statistics, compacts the results into its BS output words and stores
@@ -551,7 +565,7 @@ __host__ __device__ constexpr uint32_t lane_warp_words(int bmax, int inputs, int
 
 template <class Op, int B, int BS, int L, int MODE>
 __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t* words,
-                                        uint64_t n, uint32_t* sbuf) {
+                                        uint64_t n, uint32_t* sbuf, uint64_t* bar) {
   constexpr int S = lane_stages(B);
   constexpr int TW = 32 * B;  // words of an input tile
   constexpr int NI = Op::kTwoInputs ? 2 : 1;
@@ -567,23 +581,33 @@ __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t*
   auto slot_a = [&](uint32_t k) { return sbuf + (k % S) * NI * TW; };
   LaneWord<L> orb = 0;
   uint32_t neg = 0;
-  // cp.async ring: the next S - 1 tiles in flight while tile k is decoded
+  // bulk-copy ring: the next S - 1 tiles in flight while tile k is decoded,
+  // slot k % S completing phase (k / S) & 1 of its mbarrier
+  if (lane == 0) {
+    for (int i = 0; i < S; ++i) ax::mbar_init(&bar[i], 1);
+    ax::mbar_init_fence();
+  }
+  __syncwarp();
 #pragma unroll
   for (uint32_t k = 0; k < S - 1; ++k) {
     const uint64_t t = tile0 + k * gwarps;
-    if (t < ntiles) op.template lanes_issue<B>(t, slot_a(k), slot_a(k) + TW, lane);
-    cp_async_commit_ge();
+    if (t < ntiles) op.template lanes_fill<B>(t, slot_a(k), slot_a(k) + TW, &bar[k], lane);
   }
-  for (uint32_t k = 0;; ++k) {
+  uint32_t k = 0;
+  bool ok = true;
+  for (;; ++k) {
     const uint64_t tile = tile0 + k * gwarps;
     if (tile >= ntiles) break;
     const uint64_t tn = tile + (S - 1) * gwarps;
-    if (tn < ntiles) op.template lanes_issue<B>(tn, slot_a(k + S - 1), slot_a(k + S - 1) + TW, lane);
-    cp_async_commit_ge();
-    if constexpr (S == 3)
-      cp_async_wait2_ge();  // tile k has landed (groups complete in order)
-    else
-      cp_async_wait1_ge();
+    if (tn < ntiles) {  // slot of tile k - 1: read by every lane before the last __syncwarp
+      if (lane == 0) ax::fence_proxy_async_smem();
+      op.template lanes_fill<B>(tn, slot_a(k + S - 1), slot_a(k + S - 1) + TW,
+                                &bar[(k + S - 1) % S], lane);
+    }
+    if (!ax::mbar_wait(&bar[k % S], (k / S) & 1)) {
+      ok = false;
+      break;
+    }
     __syncwarp();
     const uint32_t* bufa = slot_a(k);
     uint32_t wa[B + 1], wb[B + 1];
@@ -634,7 +658,12 @@ __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t*
     }
     __syncwarp();
   }
-  cp_async_wait0_ge();
+  if (!ok) {  // a copy that never landed: report it, and wait (bounded) for the rest
+    if (lane == 0) set_status(out, CCM_E_TIMEOUT);
+    for (uint32_t j = 0; j < S; ++j)
+      if (tile0 + (k + j) * gwarps < ntiles) ax::mbar_wait(&bar[(k + j) % S], ((k + j) / S) & 1);
+    return;
+  }
   uint64_t o;
   if constexpr (L == 64) {
     o = warp_or64(orb);
@@ -656,34 +685,36 @@ __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t*
 // size is lane_bits(BS).
 template <class Op, int B, int BS>
 __device__ __forceinline__ void lanes_modes(const Op& op, int mode, ccm_header* out,
-                                            uint32_t* words, uint64_t n, uint32_t* sbuf) {
+                                            uint32_t* words, uint64_t n, uint32_t* sbuf,
+                                            uint64_t* bar) {
   constexpr int L = lane_bits(BS);
   if (mode == 0)
-    lanes_body<Op, B, BS, L, 0>(op, out, words, n, sbuf);
+    lanes_body<Op, B, BS, L, 0>(op, out, words, n, sbuf, bar);
   else
-    lanes_body<Op, B, BS, L, 1>(op, out, words, n, sbuf);
+    lanes_body<Op, B, BS, L, 1>(op, out, words, n, sbuf, bar);
 }
 
 template <class Op, int B, int D = 1>
 __device__ __forceinline__ void lanes_grow(const Op& op, int d, int mode, ccm_header* out,
-                                           uint32_t* words, uint64_t n, uint32_t* sbuf) {
+                                           uint32_t* words, uint64_t n, uint32_t* sbuf,
+                                           uint64_t* bar) {
   if constexpr (D <= Op::kLaneGrow) {
     if (d == D)
-      lanes_modes<Op, B, B + D>(op, mode, out, words, n, sbuf);
+      lanes_modes<Op, B, B + D>(op, mode, out, words, n, sbuf, bar);
     else
-      lanes_grow<Op, B, D + 1>(op, d, mode, out, words, n, sbuf);
+      lanes_grow<Op, B, D + 1>(op, d, mode, out, words, n, sbuf, bar);
   }
 }
 
 template <class Op, int B = 1>
 __device__ __forceinline__ void lanes_dispatch(const Op& op, int b, int bs, int mode,
                                                ccm_header* out, uint32_t* words, uint64_t n,
-                                               uint32_t* sbuf) {
+                                               uint32_t* sbuf, uint64_t* bar) {
   if constexpr (B <= 32) {
     if (b == B)
-      lanes_grow<Op, B>(op, bs - B, mode, out, words, n, sbuf);
+      lanes_grow<Op, B>(op, bs - B, mode, out, words, n, sbuf, bar);
     else
-      lanes_dispatch<Op, B + 1>(op, b, bs, mode, out, words, n, sbuf);
+      lanes_dispatch<Op, B + 1>(op, b, bs, mode, out, words, n, sbuf, bar);
   }
 }
 
@@ -694,6 +725,7 @@ __global__ void __launch_bounds__(kThreads) k_ew_lanes(Op op, ccm_header* out, u
                                                        uint64_t capacity, uint64_t n,
                                                        uint32_t warp_words) {
   extern __shared__ __align__(16) uint32_t s_lanes[];
+  __shared__ uint64_t s_lane_bar[kWarps][3];
   if (out->status != CCM_OK) return;
   op.init(n);
   const int bs = op.spec_width();
@@ -706,7 +738,8 @@ __global__ void __launch_bounds__(kThreads) k_ew_lanes(Op op, ccm_header* out, u
     out->reserved0 = bs;  // ... at this (speculative) width
   }
   lanes_dispatch<Op>(op, B, bs, op.lanes_mode(), out, words, n,
-                     s_lanes + (threadIdx.x / kWarp) * warp_words);
+                     s_lanes + (threadIdx.x / kWarp) * warp_words,
+                     s_lane_bar[threadIdx.x / kWarp]);
 }
 
 // Host launchers (ew_lanes.cu).

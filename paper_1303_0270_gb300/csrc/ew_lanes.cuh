@@ -20,7 +20,10 @@ static void launch_lanes(const Op& op, ccm_header* out, uint32_t* words, uint64_
   if (dev_done != dev) {
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncSetAttribute(k_ew_lanes<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, k_ew_lanes<Op>);  // (its static mbarriers count against optin)
+    cudaFuncSetAttribute(k_ew_lanes<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         optin - (int)fa.sharedSizeBytes);
     dev_done = dev;
   }
   int per_sm = 0;
