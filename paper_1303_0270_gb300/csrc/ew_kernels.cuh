@@ -298,6 +298,70 @@ __device__ __forceinline__ uint64_t offset_out64(uint64_t r, uint64_t& orb, uint
   return r ^ top;
 }
 
+// Slot form of the lane pass (results of BS <= 32 bits): KS = 32 / BS
+// fields of a lane's group side by side in one 32-bit word, field j in bits
+// [j BS, j BS + BS), so that the sum (or the scaled value) of a word of
+// slots is one add (one multiply-add) and lands already packed at width BS.
+// expand_slots moves K consecutive B-bit fields (bits [j B, j B + B)) into
+// the slots: log2 K steps, highest first, each moving the fields whose index
+// has bit p set by p (BS - B) bits with one AND and one multiply-add,
+// x + (x & m) (2^d - 1) = (x & ~m) + ((x & m) << d), which runs on the FMA
+// pipe beside the integer one.
+__host__ __device__ constexpr int slot_fields(int bs) { return 32 / bs; }
+
+__host__ __device__ constexpr uint32_t slot_ones(int bs, int k) {
+  uint32_t m = 0;
+  for (int j = 0; j < k; ++j) m |= 1u << (j * bs);
+  return m;
+}
+
+// Bits of the fields moved at step p (their positions before the step).
+__host__ __device__ constexpr uint32_t slot_move_mask(int b, int g, int k, int p) {
+  uint32_t m = 0;
+  for (int j = 0; j < k; ++j)
+    if (j & p) m |= ((1u << b) - 1u) << (j * b + (j & ~(2 * p - 1)) * g);
+  return m;
+}
+
+__host__ __device__ constexpr int top_pow2(int v) {
+  int p = v >= 1 ? 1 : 0;
+  while (p && p * 2 <= v) p *= 2;
+  return p;
+}
+
+template <int B, int G, int K, int P>
+__device__ __forceinline__ uint32_t expand_steps(uint32_t x) {
+  if constexpr (P == 0) {
+    return x;
+  } else {
+    constexpr uint32_t m = slot_move_mask(B, G, K, P);
+    constexpr uint32_t f = (1u << (P * G)) - 1u;
+    return expand_steps<B, G, K, P / 2>((x & m) * f + x);
+  }
+}
+
+// Fields c K .. c K + K - 1 of a lane's B-bit group (words w, w[B] = 0) in
+// slots of B + G bits.
+template <int B, int G, int K>
+__device__ __forceinline__ uint32_t expand_slots(const uint32_t* w, int first) {
+  const int bit = B * first, wi = bit >> 5, sh = bit & 31;
+  const uint32_t x = sh + K * B <= 32 ? (w[wi] >> sh) : __funnelshift_r(w[wi], w[wi + 1], sh);
+  return expand_steps<B, G, K, top_pow2(K - 1)>(x & ((1u << (K * B)) - 1u));  // K B < 32
+}
+
+// offset_out for K slots of BS bits.
+template <int BS, int K>
+__device__ __forceinline__ uint32_t offset_out_slots(uint32_t r, uint32_t& orb, uint32_t& neg) {
+  constexpr uint32_t ones = slot_ones(BS, K);
+  constexpr uint32_t lo1 = (1u << (BS - 1)) - 1u;
+  constexpr uint32_t lo = lo1 * ones;
+  constexpr uint32_t top = (1u << (BS - 1)) * ones;
+  const uint32_t pos = ((r >> (BS - 1)) & ones) * lo1;  // slots with c >= 0
+  orb |= (r ^ lo ^ pos) & lo;
+  neg |= ~r & top;
+  return r ^ top;
+}
+
 // Bytes fill_tile brings for tile `tile` of input x at width B.
 template <int B>
 __device__ __forceinline__ uint32_t lanes_fill_bytes(const PackedIn& x, uint64_t tile) {
@@ -338,6 +402,25 @@ struct OpAdd {
   template <int B, int BS, int L, int MODE>
   __device__ __forceinline__ LaneConst lanes_const() const {
     return {};
+  }
+  struct SlotConst {};
+  template <int B, int BS, int KS, int KL, int MODE>
+  __device__ __forceinline__ SlotConst slots_const() const {
+    return {};
+  }
+  // Fields first .. first + K - 1 in slot form: the sums, with the
+  // statistics (offset binary for signed operands, as in lanes_k).
+  template <int B, int BS, int K, bool LAST, int MODE>
+  __device__ __forceinline__ uint32_t slots_k(const uint32_t* wa, const uint32_t* wb, int first,
+                                              uint32_t& orb, uint32_t& neg,
+                                              const SlotConst&) const {
+    const uint32_t r = expand_slots<B, BS - B, K>(wa, first) + expand_slots<B, BS - B, K>(wb, first);
+    if constexpr (MODE == 0) {
+      orb |= r;
+      return r;
+    } else {
+      return offset_out_slots<BS, K>(r, orb, neg);
+    }
   }
   // Chunk c of the lane's group: the sums, one per lane, as the output
   // field bits (width BS = B + 1), with the statistics of the result.
@@ -472,6 +555,41 @@ struct OpScale {
       return {t, s < 0 ? (uint32_t)lob * ones : 0u, p * ones};
     }
   }
+  // Slot form: t, the complement masks and P per word of KS slots (the
+  // chunks) and of KL slots (the last chunk of a group).
+  struct SlotConst {
+    uint32_t t, cm_k, cm_l, p_k, p_l;
+  };
+  template <int B, int BS, int KS, int KL, int MODE>
+  __device__ __forceinline__ SlotConst slots_const() const {
+    constexpr uint32_t lob = B >= 32 ? ~0u : (1u << B) - 1u;
+    const uint32_t t = (uint32_t)(s < 0 ? -s : s);
+    if constexpr (MODE == 0 || BS > 32) {  // (BS > 32: the 64-bit lanes, not slots)
+      return {t, 0u, 0u, 0u, 0u};
+    } else {
+      const uint32_t half = 1u << (BS - 1);
+      const uint32_t p = !a.sgn ? half - t * lob
+                         : s > 0 ? half - t * (1u << (B - 1))
+                                 : half - t * ((1u << (B - 1)) - 1u);
+      const bool c = s < 0;
+      return {t, c ? lob * slot_ones(BS, KS) : 0u, c ? lob * slot_ones(BS, KL) : 0u,
+              p * slot_ones(BS, KS), p * slot_ones(BS, KL)};
+    }
+  }
+  template <int B, int BS, int K, bool LAST, int MODE>
+  __device__ __forceinline__ uint32_t slots_k(const uint32_t* wa, const uint32_t*, int first,
+                                              uint32_t& orb, uint32_t& neg,
+                                              const SlotConst& kc) const {
+    const uint32_t v = expand_slots<B, BS - B, K>(wa, first);
+    if constexpr (MODE == 0) {
+      const uint32_t r = v * kc.t;
+      orb |= r;
+      return r;
+    } else {
+      const uint32_t cm = LAST ? kc.cm_l : kc.cm_k, p = LAST ? kc.p_l : kc.p_k;
+      return offset_out_slots<BS, K>((v ^ cm) * kc.t + p, orb, neg);
+    }
+  }
   template <int B, int BS, int L, int MODE>
   __device__ __forceinline__ LaneWord<L> lanes_k(const uint32_t* wa, const uint32_t*, int c,
                                                  LaneWord<L>& orb, uint32_t& neg,
@@ -569,8 +687,11 @@ __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t*
   constexpr int S = lane_stages(B);
   constexpr int TW = 32 * B;  // words of an input tile
   constexpr int NI = Op::kTwoInputs ? 2 : 1;
-  constexpr int K = L == 64 ? 1 : 32 / L;  // fields per register (per 64-bit value)
+  // slot form (BS <= 32): KS fields per chunk, NC chunks, KL in the last
+  constexpr int KS = L == 64 ? 1 : slot_fields(BS);
+  constexpr int NC = (32 + KS - 1) / KS, KL = 32 - (NC - 1) * KS;
   const typename Op::LaneConst kc = op.template lanes_const<B, BS, L, MODE>();
+  const typename Op::SlotConst sc = op.template slots_const<B, BS, KS, KL, MODE>();
   const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
   const uint64_t dw = data_words(n, BS);
   const uint64_t ntiles = (n + kTile - 1) / kTile;
@@ -579,7 +700,8 @@ __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t*
   // per warp: S slots of (A tile[, B tile]), then the output tile
   uint32_t* obuf = sbuf + S * NI * TW;
   auto slot_a = [&](uint32_t k) { return sbuf + (k % S) * NI * TW; };
-  LaneWord<L> orb = 0;
+  LaneWord<L> orb = 0;  // (the 64-bit path)
+  uint32_t orb32 = 0;   // (slot form)
   uint32_t neg = 0;
   // bulk-copy ring: the next S - 1 tiles in flight while tile k is decoded,
   // slot k % S completing phase (k / S) & 1 of its mbarrier
@@ -628,18 +750,28 @@ __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t*
     uint32_t ow[BS + 1];
 #pragma unroll
     for (int i = 0; i <= BS; ++i) ow[i] = 0;
+    if constexpr (L == 64) {
 #pragma unroll
-    for (int c = 0; c < 32 / K; ++c) {
-      const LaneWord<L> r = op.template lanes_k<B, BS, L, MODE>(wa, wb, c, orb, neg, kc);
-      const int bit = K * BS * c, wi = bit >> 5, sh = bit & 31;
-      if constexpr (L == 64) {  // one field of 33..36 bits: up to three words
+      for (int c = 0; c < 32; ++c) {  // one field of 33..36 bits: up to three words
+        const LaneWord<L> r = op.template lanes_k<B, BS, L, MODE>(wa, wb, c, orb, neg, kc);
+        const int bit = BS * c, wi = bit >> 5, sh = bit & 31;
         ow[wi] |= (uint32_t)(r << sh);
         if (sh + BS > 32) ow[wi + 1] |= (uint32_t)(r >> (32 - sh));
         if (sh + BS > 64) ow[wi + 2] |= (uint32_t)(r >> (64 - sh));
-      } else {
-        const uint32_t t = compact_l<BS, L>(r);
-        ow[wi] |= t << sh;
-        if (sh + K * BS > 32) ow[wi + 1] |= t >> (32 - sh);
+      }
+    } else {
+      // slot form: KS fields per chunk (KL in the last), each chunk's word of
+      // slots placed at its bit offset with a shift-add and a high multiply
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        uint32_t r;
+        if (c == NC - 1)
+          r = op.template slots_k<B, BS, KL, true, MODE>(wa, wb, c * KS, orb32, neg, sc);
+        else
+          r = op.template slots_k<B, BS, KS, false, MODE>(wa, wb, c * KS, orb32, neg, sc);
+        const int bit = KS * BS * c, wi = bit >> 5, sh = bit & 31;
+        ow[wi] += r << sh;
+        if (sh + KS * BS > 32) ow[wi + 1] += __umulhi(r, 1u << sh);  // r >> (32 - sh)
       }
     }
     sts_words<BS>(obuf, lane * BS, ow);
@@ -668,9 +800,10 @@ __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t*
   if constexpr (L == 64) {
     o = warp_or64(orb);
   } else {
-    uint32_t o32 = orb;
-    if constexpr (L == 8) o32 = (o32 | (o32 >> 8) | (o32 >> 16) | (o32 >> 24)) & 0xffu;
-    if constexpr (L == 16) o32 = (o32 | (o32 >> 16)) & 0xffffu;
+    constexpr uint32_t slot = BS >= 32 ? ~0u : (1u << BS) - 1u;
+    uint32_t o32 = 0;
+#pragma unroll
+    for (int j = 0; j < KS; ++j) o32 |= (orb32 >> (j * BS)) & slot;
     o = __reduce_or_sync(0xffffffffu, o32);
   }
   const uint32_t ng = __reduce_or_sync(0xffffffffu, neg);
