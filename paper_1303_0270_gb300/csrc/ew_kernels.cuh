@@ -148,66 +148,6 @@ __device__ __forceinline__ uint32_t PackedIn::fill_tile(uint64_t tile, uint32_t*
   return 4 * cw;
 }
 
-// Byte lanes: four fields of at most 8 bits in one 32-bit register, field k
-// in byte k.  spread_c<B> moves four consecutive B-bit fields there,
-// compact_c<C> moves byte k back to bits [k C, (k + 1) C); both in two
-// steps (pairs of fields into 16-bit halves, then fields into bytes) with
-// shifts and masks fixed at compile time.
-template <int B>
-__device__ __forceinline__ uint32_t spread_c(const uint32_t* w, int c) {
-  const int bit = 4 * B * c, wi = bit >> 5, sh = bit & 31;
-  const uint32_t x = sh + 4 * B <= 32 ? (w[wi] >> sh) : __funnelshift_r(w[wi], w[wi + 1], sh);
-  constexpr uint32_t m2 = (1u << (2 * B)) - 1u;
-  constexpr uint32_t m1 = ((1u << B) - 1u) * 0x00010001u;
-  const uint32_t u = (x & m2) | ((x << (16 - 2 * B)) & (m2 << 16));
-  return (u & m1) | ((u << (8 - B)) & (m1 << 8));
-}
-
-template <int C>
-__device__ __forceinline__ uint32_t compact_c(uint32_t v) {
-  constexpr uint32_t m1 = ((1u << C) - 1u) * 0x00010001u;
-  constexpr uint32_t m1b = (((1u << C) - 1u) << C) * 0x00010001u;
-  constexpr uint32_t m2 = (1u << (2 * C)) - 1u;
-  const uint32_t u = (v & m1) | ((v >> (8 - C)) & m1b);
-  return (u & m2) | ((u >> (16 - 2 * C)) & (m2 << (2 * C)));
-}
-
-// Lanes of L = 8, 16 or 32 bits: K = 32 / L fields per register.  spread_l
-// moves the K fields of chunk c (fields K c .. K c + K - 1 of a B-bit group)
-// into the lanes; compact_l is the inverse at width C.
-template <int L>
-__host__ __device__ constexpr uint32_t lane_ones() {
-  return L == 8 ? 0x01010101u : (L == 16 ? 0x00010001u : 1u);
-}
-
-template <int B, int L>
-__device__ __forceinline__ uint32_t spread_l(const uint32_t* w, int c) {
-  if constexpr (L == 8) {
-    return spread_c<B>(w, c);
-  } else {
-    constexpr int K = 32 / L;
-    constexpr uint32_t lo = B >= 32 ? ~0u : (1u << B) - 1u;
-    const int bit = K * B * c, wi = bit >> 5, sh = bit & 31;
-    const uint32_t x = sh + K * B <= 32 ? (w[wi] >> sh) : __funnelshift_r(w[wi], w[wi + 1], sh);
-    if constexpr (L == 16)
-      return (x & lo) | ((x << (16 - B)) & (lo << 16));
-    else
-      return x & lo;
-  }
-}
-
-template <int C, int L>
-__device__ __forceinline__ uint32_t compact_l(uint32_t v) {
-  if constexpr (L == 8) {
-    return compact_c<C>(v);
-  } else if constexpr (L == 16) {
-    constexpr uint32_t lo = (1u << C) - 1u;
-    return (v & lo) | ((v >> (16 - C)) & (lo << C));
-  } else {
-    return v;
-  }
-}
-
 // NW consecutive shared words from word w0 (w0 a multiple of the vector
 // width chosen: 4 words when NW % 4 == 0, else 2 when even, else 1).
 template <int NW>
@@ -255,30 +195,8 @@ __device__ __forceinline__ void sts_words(uint32_t* buf, int w0, const uint32_t*
 // zero bits above the last field (a packed matrix is canonical) or from the
 // zero fill of words past the end, and give 0 in every operation.
 // ---------------------------------------------------------------------------
-// Lane results r in offset binary at width BS (r = c + 2^(BS-1), every lane
-// below 2^BS): c >= 0 exactly when bit BS - 1 of the lane is set; returns the
-// two's complement bits of c (r ^ 2^(BS-1)) and ORs the folded values
-// (c >= 0 ? c : ~c, the bits below BS - 1) into `orb`, the sign into `neg`.
-template <int BS, int L>
-__device__ __forceinline__ uint32_t offset_out(uint32_t r, uint32_t& orb, uint32_t& neg) {
-  constexpr uint32_t ones = lane_ones<L>();
-  constexpr uint32_t lo1 = BS - 1 >= 32 ? ~0u : (1u << (BS - 1)) - 1u;
-  constexpr uint32_t lo = lo1 * ones;
-  constexpr uint32_t top = (1u << (BS - 1)) * ones;
-  const uint32_t pos = ((r >> (BS - 1)) & ones) * lo1;  // lanes with c >= 0
-  orb |= (r ^ lo ^ pos) & lo;
-  neg |= ~r & top;
-  return r ^ top;
-}
-
-// Lane size (bits) that holds a BS-bit result: 8, 16 or 32 bits (4, 2 or 1
-// fields per 32-bit register), or 64 (one field per 64-bit value) for the
-// results of 33..36 bits.
-__host__ __device__ constexpr int lane_bits(int bs) {
-  return bs <= 8 ? 8 : (bs <= 16 ? 16 : (bs <= 32 ? 32 : 64));
-}
-template <int L>
-using LaneWord = typename std::conditional<(L == 64), uint64_t, uint32_t>::type;
+// Results of 33..36 bits (the sum of two 32-bit operands, a scaled 32-bit
+// one) take one 64-bit value per field; narrower ones the slot form below.
 
 // Field c (B <= 32 bits) of a lane's group, zero-extended to 64 bits.
 template <int B>
@@ -288,7 +206,10 @@ __device__ __forceinline__ uint64_t spread64(const uint32_t* w, int c) {
   return (uint64_t)(B >= 32 ? x : (x & ((1u << B) - 1u)));
 }
 
-// offset_out for a 64-bit lane (BS = 33..36).
+// A result r in offset binary at width BS = 33..36 (r = c + 2^(BS-1)):
+// c >= 0 exactly when bit BS - 1 is set; returns the two's complement bits
+// of c (r ^ 2^(BS-1)) and ORs the folded value (c >= 0 ? c : ~c, the bits
+// below BS - 1) into `orb`, the sign into `neg`.
 template <int BS>
 __device__ __forceinline__ uint64_t offset_out64(uint64_t r, uint64_t& orb, uint32_t& neg) {
   constexpr uint64_t lo = (1ull << (BS - 1)) - 1ull, top = 1ull << (BS - 1);
@@ -399,7 +320,7 @@ struct OpAdd {
   // Mask of the sign-bit XOR on the inputs in mode 1 (all of them here).
   __device__ __forceinline__ uint32_t lanes_in_xor() const { return ~0u; }
   struct LaneConst {};
-  template <int B, int BS, int L, int MODE>
+  template <int B, int BS, int MODE>
   __device__ __forceinline__ LaneConst lanes_const() const {
     return {};
   }
@@ -422,34 +343,23 @@ struct OpAdd {
       return offset_out_slots<BS, K>(r, orb, neg);
     }
   }
-  // Chunk c of the lane's group: the sums, one per lane, as the output
-  // field bits (width BS = B + 1), with the statistics of the result.
-  // Signed inputs arrive in offset binary (u = a + 2^(B-1)), so
-  // u_a + u_b = c + 2^B is the sum in offset binary at width B + 1.
-  template <int B, int BS, int L, int MODE>
-  __device__ __forceinline__ LaneWord<L> lanes_k(const uint32_t* wa, const uint32_t* wb, int c,
-                                                 LaneWord<L>& orb, uint32_t& neg,
-                                                 const LaneConst&) const {
-    if constexpr (L == 64) {
-      const uint64_t sum = spread64<B>(wa, c) + spread64<B>(wb, c);
-      if constexpr (MODE == 0) {
-        orb |= sum;
-        return sum;
-      } else {
-        return offset_out64<BS>(sum, orb, neg);
-      }
+  // Field c of the lane's group when the sum has 33 bits (B = 32): the sum
+  // in a 64-bit value with the statistics of the result.  Signed inputs
+  // arrive in offset binary (u = a + 2^(B-1)), so u_a + u_b = c + 2^B is the
+  // sum in offset binary at width B + 1.
+  template <int B, int BS, int MODE>
+  __device__ __forceinline__ uint64_t lanes_k(const uint32_t* wa, const uint32_t* wb, int c,
+                                              uint64_t& orb, uint32_t& neg,
+                                              const LaneConst&) const {
+    const uint64_t sum = spread64<B>(wa, c) + spread64<B>(wb, c);
+    if constexpr (MODE == 0) {
+      orb |= sum;
+      return sum;
     } else {
-      const uint32_t sum = spread_l<B, L>(wa, c) + spread_l<B, L>(wb, c);
-      if constexpr (MODE == 0) {
-        orb |= sum;
-        return sum;
-      } else {
-        return offset_out<BS, L>(sum, orb, neg);
-      }
+      return offset_out64<BS>(sum, orb, neg);
     }
   }
   static constexpr bool kTwoInputs = true;
-  // cp.async of tile `tile` of both inputs into plain-order shared buffers
   // tile `tile` of both inputs into plain-order shared buffers, one bulk
   // copy each on `bar` (lane 0 arms it with the bytes of both)
   template <int B>
@@ -510,17 +420,17 @@ struct OpScale {
     if (lo < -lim || hi >= lim) return 65;
     return range_width((int64_t)lo, (int64_t)hi);
   }
-  // Lanes apply for 1 <= |s| < 2^5, A of at most 31 bits and a speculative
-  // width BS = B + D with 1 <= D <= kLaneGrow and B + bitlen|s| at most the
-  // lane size of BS (so that no lane product carries into the next lane),
-  // except 1-bit signed A with s < 0 (values {-1, 0}: a non-negative result
-  // range, not the signed one mode 1 writes).  Returns B (0: not applicable).
+  // Lanes apply for 1 <= |s| < 2^5, A of at most 32 bits and a speculative
+  // width BS = B + D with 1 <= D <= kLaneGrow (every result then fits its
+  // BS-bit slot, or its 64-bit value), except 1-bit signed A with s < 0
+  // (values {-1, 0}: a non-negative result range, not the signed one mode 1
+  // writes).  Returns B (0: not applicable).
   static constexpr int kLaneGrow = 4;
   __device__ __forceinline__ int lanes_width(int bs) const {
     const int64_t t = s < 0 ? -s : s;
     if (t < 1 || t >= 32 || a.b > 32 || bs - a.b < 1 || bs - a.b > kLaneGrow) return 0;
     if (a.sgn && a.b == 1 && s < 0) return 0;
-    return a.b + bitlen64((uint64_t)t) <= lane_bits(bs) ? a.b : 0;
+    return a.b;
   }
   // Lane mode: 0 unsigned A and s > 0 (unsigned result); 1 signed A, or
   // unsigned A and s < 0 (offset binary out; the sign-bit XOR on the input
@@ -534,15 +444,14 @@ struct OpScale {
   //   signed, s < 0:   c = t v - t (2^(B-1) - 1),  P = 2^(BS-1) - t (2^(B-1) - 1)
   //   unsigned, s < 0: c = t v - t (2^B - 1),      P = 2^(BS-1) - t (2^B - 1)
   // (mode 0: r = t a, P = 0; mode 1: the other three).  BS is the width of s times A's range, so every
-  // r lies in [0, 2^BS) and every t v below 2^L: one multiply and one add
-  // per register of lanes, no carry between lanes.
-  struct LaneConst {
-    uint32_t t, cmask;  // |s|; the complement mask per register (s < 0)
-    uint64_t p;         // P per register (per 64-bit value when L = 64)
+  // r lies in [0, 2^BS): one multiply and one add per word of slots (per
+  // 64-bit value for BS > 32), no carry from one slot into the next.
+  struct LaneConst {  // the 64-bit values (BS = 33..36)
+    uint32_t t, cmask;  // |s|; the complement mask (s < 0)
+    uint64_t p;         // P
   };
-  template <int B, int BS, int L, int MODE>
+  template <int B, int BS, int MODE>
   __device__ __forceinline__ LaneConst lanes_const() const {
-    constexpr uint32_t ones = L == 64 ? 1u : lane_ones<L>();
     constexpr uint64_t lob = (1ull << B) - 1ull;
     const uint32_t t = (uint32_t)(s < 0 ? -s : s);
     if constexpr (MODE == 0) {
@@ -552,7 +461,7 @@ struct OpScale {
       const uint64_t p = !a.sgn ? half - t * lob
                          : s > 0 ? half - t * (1ull << (B - 1))
                                  : half - t * ((1ull << (B - 1)) - 1ull);
-      return {t, s < 0 ? (uint32_t)lob * ones : 0u, p * ones};
+      return {t, s < 0 ? (uint32_t)lob : 0u, p};
     }
   }
   // Slot form: t, the complement masks and P per word of KS slots (the
@@ -590,28 +499,18 @@ struct OpScale {
       return offset_out_slots<BS, K>((v ^ cm) * kc.t + p, orb, neg);
     }
   }
-  template <int B, int BS, int L, int MODE>
-  __device__ __forceinline__ LaneWord<L> lanes_k(const uint32_t* wa, const uint32_t*, int c,
-                                                 LaneWord<L>& orb, uint32_t& neg,
-                                                 const LaneConst& kc) const {
-    if constexpr (L == 64) {
-      const uint64_t v = spread64<B>(wa, c);
-      if constexpr (MODE == 0) {
-        const uint64_t r = v * kc.t;
-        orb |= r;
-        return r;
-      } else {
-        return offset_out64<BS>((v ^ kc.cmask) * kc.t + kc.p, orb, neg);
-      }
+  // Field c of the lane's group scaled, for BS = 33..36 (a 64-bit value).
+  template <int B, int BS, int MODE>
+  __device__ __forceinline__ uint64_t lanes_k(const uint32_t* wa, const uint32_t*, int c,
+                                              uint64_t& orb, uint32_t& neg,
+                                              const LaneConst& kc) const {
+    const uint64_t v = spread64<B>(wa, c);
+    if constexpr (MODE == 0) {
+      const uint64_t r = v * kc.t;
+      orb |= r;
+      return r;
     } else {
-      const uint32_t v = spread_l<B, L>(wa, c);
-      if constexpr (MODE == 0) {
-        const uint32_t r = v * kc.t;
-        orb |= r;
-        return r;
-      } else {
-        return offset_out<BS, L>((v ^ kc.cmask) * kc.t + (uint32_t)kc.p, orb, neg);
-      }
+      return offset_out64<BS>((v ^ kc.cmask) * kc.t + kc.p, orb, neg);
     }
   }
   static constexpr bool kTwoInputs = false;
@@ -653,15 +552,16 @@ constexpr int kStats = 0, kPack = 1, kSpec = 2;
 // when the operands qualify (Op::lanes_width, decided from the headers), it
 // does the pass and marks the output header (reserved1 = 1) so that the
 // general kSpec launch returns at once; otherwise it returns and the general
-// pass runs.  Input width B, output width BS, lane size L (8, 16 or 32 bits:
-// four, two or one field per register) and sign mode are compile-time.
-// Per tile the inputs are staged in plain word order through a ring of
-// bulk copies (one per input tile, issued by lane 0 on the slot's mbarrier,
-// waits bounded); each lane reads its group's B words with the widest aligned vector
-// (signed inputs: XOR of the sign bits), forms the results a register of
-// lanes at a time (one add or multiply for 4, 2 or 1 fields), ORs the
-// statistics, compacts the results into its BS output words and stores
-// those; the warp then writes the output tile with 16-byte stores.
+// pass runs.  Input width B, output width BS (slot form for BS <= 32, one
+// 64-bit value per field above) and sign mode are compile-time.  Per tile
+// the inputs are staged in plain word order through a ring of bulk copies
+// (one per input tile, issued by lane 0 on the slot's mbarrier, waits
+// bounded); each lane reads its group's B words with the widest aligned
+// vector (signed inputs: XOR of the sign bits), forms the results a word of
+// slots at a time (one add, or one multiply-add, for 32 / BS fields), ORs the
+// statistics, places each word at its bit offset among its BS output words
+// and stores those; the warp then writes the output tile with 16-byte
+// stores.
 __host__ __device__ constexpr int lane_stages(int B) { return B <= 8 ? 3 : 2; }
 
 // Shared words per warp of the pass at input width b and output width bs
@@ -690,7 +590,7 @@ __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t*
   // slot form (BS <= 32): KS fields per chunk, NC chunks, KL in the last
   constexpr int KS = L == 64 ? 1 : slot_fields(BS);
   constexpr int NC = (32 + KS - 1) / KS, KL = 32 - (NC - 1) * KS;
-  const typename Op::LaneConst kc = op.template lanes_const<B, BS, L, MODE>();
+  const typename Op::LaneConst kc = op.template lanes_const<B, BS, MODE>();
   const typename Op::SlotConst sc = op.template slots_const<B, BS, KS, KL, MODE>();
   const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
   const uint64_t dw = data_words(n, BS);
@@ -700,7 +600,7 @@ __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t*
   // per warp: S slots of (A tile[, B tile]), then the output tile
   uint32_t* obuf = sbuf + S * NI * TW;
   auto slot_a = [&](uint32_t k) { return sbuf + (k % S) * NI * TW; };
-  LaneWord<L> orb = 0;  // (the 64-bit path)
+  uint64_t orb = 0;     // (the 64-bit path)
   uint32_t orb32 = 0;   // (slot form)
   uint32_t neg = 0;
   // bulk-copy ring: the next S - 1 tiles in flight while tile k is decoded,
@@ -753,7 +653,7 @@ __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t*
     if constexpr (L == 64) {
 #pragma unroll
       for (int c = 0; c < 32; ++c) {  // one field of 33..36 bits: up to three words
-        const LaneWord<L> r = op.template lanes_k<B, BS, L, MODE>(wa, wb, c, orb, neg, kc);
+        const uint64_t r = op.template lanes_k<B, BS, MODE>(wa, wb, c, orb, neg, kc);
         const int bit = BS * c, wi = bit >> 5, sh = bit & 31;
         ow[wi] |= (uint32_t)(r << sh);
         if (sh + BS > 32) ow[wi + 1] |= (uint32_t)(r >> (32 - sh));
@@ -814,13 +714,13 @@ __device__ __noinline__ void lanes_body(const Op& op, ccm_header* out, uint32_t*
 }
 
 // Calls lanes_body for the run-time (b, bs, mode).  Add: B <= 32 with
-// BS = B + 1; scale: B <= 32 with BS = B + D, 1 <= D <= kLaneGrow.  The lane
-// size is lane_bits(BS).
+// BS = B + 1; scale: B <= 32 with BS = B + D, 1 <= D <= kLaneGrow.  L = 64:
+// one 64-bit value per field (BS > 32); L = 32: the slot form.
 template <class Op, int B, int BS>
 __device__ __forceinline__ void lanes_modes(const Op& op, int mode, ccm_header* out,
                                             uint32_t* words, uint64_t n, uint32_t* sbuf,
                                             uint64_t* bar) {
-  constexpr int L = lane_bits(BS);
+  constexpr int L = BS > 32 ? 64 : 32;
   if (mode == 0)
     lanes_body<Op, B, BS, L, 0>(op, out, words, n, sbuf, bar);
   else

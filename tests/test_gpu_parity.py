@@ -416,13 +416,12 @@ def _range_width(lo, hi):
 
 def _scale_lanes_expected(b, sgn, s, bs):
     """Whether the scale lane pass applies: 1 <= |s| < 32, A of at most 32
-    bits, 1 <= bs - b <= 4, b + bitlen|s| at most the lane size of bs (8, 16,
-    32, or 64 bits for 33..36-bit results), and not 1-bit signed A with
+    bits, 1 <= bs - b <= 4 (every result then fits its bs-bit slot, or its
+    64-bit value for 33..36-bit results), and not 1-bit signed A with
     s < 0."""
     t = abs(s)
-    lane = 8 if bs <= 8 else (16 if bs <= 16 else (32 if bs <= 32 else 64))
     return 1 <= t < 32 and b <= 32 and 1 <= bs - b <= 4 and \
-        b + t.bit_length() <= lane and not (sgn and b == 1 and s < 0)
+        not (sgn and b == 1 and s < 0)
 
 
 @pytest.mark.parametrize("b,sgn", [(1, 0), (1, 1), (3, 0), (5, 0), (7, 1), (8, 1), (12, 1),
