@@ -6,6 +6,7 @@
 
 #include "kernels.h"
 #include "matvec_stream.cuh"
+#include "cta_pack.cuh"
 #include "pack_engine.cuh"
 
 namespace ccm {
@@ -127,35 +128,7 @@ __global__ void __launch_bounds__(kYThreads) k_mv_ypack(ccm_header* out, uint32_
     if (nw > capacity) out->status = CCM_E_CAPACITY;
   }
   if (nw > capacity) return;
-  // group g (32 fields = b words) to warp g mod 32: lane i assembles words
-  // i and i + 32 of the group from the fields that overlap them
-  const uint64_t mask = field_mask(b);
-  const uint32_t groups = (mm + 31) / 32;
-  int flo[2], fhi[2];  // fields overlapping word i (and i + 32) of a group
-  for (int h = 0; h < 2; ++h) {
-    const int wi = lane + 32 * h;
-    flo[h] = wi * 32 / b;
-    fhi[h] = (wi * 32 + 31) / b;
-  }
-  for (uint32_t g = warp; g < groups; g += kYThreads / 32) {
-    const uint32_t nf = umin(32, mm - g * 32);
-    const uint32_t nwg = (uint32_t)((nf * (uint64_t)b + 31) / 32);  // words of this group
-    const uint64_t* src = ys + g * 33;
-    for (int h = 0; h < 2; ++h) {
-      const uint32_t wi = lane + 32 * h;
-      if (wi >= nwg) continue;
-      uint32_t acc = 0;
-      const int fe = fhi[h] < (int)nf - 1 ? fhi[h] : (int)nf - 1;
-      for (int f = flo[h]; f <= fe; ++f) {
-        const int o = f * b - (int)wi * 32;  // field start relative to the word
-        const uint64_t pat = src[f] & mask;
-        acc |= o >= 0 ? (uint32_t)(pat << o) : (uint32_t)(pat >> (-o));
-      }
-      words[(uint64_t)g * b + wi] = acc;
-    }
-  }
-  // the zero pad words after the data words
-  for (uint64_t W = dw + threadIdx.x; W < nw; W += kYThreads) words[W] = 0;
+  cta_pack_groups(ys, mm, b, words, dw, nw);
 }
 
 std::mutex g_attr_mutex;
