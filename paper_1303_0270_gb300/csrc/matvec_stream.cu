@@ -14,7 +14,6 @@ namespace mvs {
 namespace {
 
 constexpr int kInitThreads = 256;
-constexpr int kYThreads = 1024;
 
 // Validates A and x (the status goes into y's header), initialises y's
 // header, clears the int64 sums and decodes x into the image k_mv reads: per
@@ -70,55 +69,24 @@ __global__ void __launch_bounds__(kInitThreads) k_mv_init(Args a) {
 }
 
 // y's width (statistics of the int64 sums), header, and y packed at that
-// width, by one CTA.  The sums are read once into shared memory, 33 slots per
-// 32-field group; a 32-field group is b whole words, and lane i of the warp
-// that takes the group assembles its words i and i + 32 from the fields that
-// overlap them (no word is written twice).
-__global__ void __launch_bounds__(kYThreads) k_mv_ypack(ccm_header* out, uint32_t* words,
-                                                        uint64_t capacity,
-                                                        const int64_t* __restrict__ y,
-                                                        uint64_t m) {
-  extern __shared__ uint64_t ys[];
-  __shared__ uint64_t s_or[kYThreads / 32];
-  __shared__ uint32_t s_neg[kYThreads / 32];
+// width, by vec_pack_ctas(m) CTAs: each reads all the sums for the
+// statistics and packs its own 16 groups of 32 fields (cta_pack.cuh); CTA 0
+// writes the header.
+__global__ void __launch_bounds__(kVecThreads) k_mv_ypack(ccm_header* out, uint32_t* words,
+                                                          uint64_t capacity,
+                                                          const int64_t* __restrict__ y,
+                                                          uint64_t m) {
+  __shared__ VecPackSmem sm;
   ax::grid_dep_wait();  // every sum of k_mv is in place
   if (out->status != CCM_OK) return;
   const uint32_t mm = (uint32_t)m;  // <= kYSmallRows
-  uint64_t orv = 0;
-  uint32_t neg = 0;
-  // loads in batches of 8 per thread, all in flight together
-  for (uint32_t base = 0; base < mm; base += 8 * kYThreads) {
-    int64_t v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const uint32_t i = base + j * kYThreads + threadIdx.x;
-      v[j] = i < mm ? y[i] : 0;
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const uint32_t i = base + j * kYThreads + threadIdx.x;
-      if (i < mm) ys[(i >> 5) * 33 + (i & 31)] = (uint64_t)v[j];
-      orv |= fold(v[j]);
-      neg |= (uint32_t)(v[j] < 0);
-    }
-  }
-  orv = warp_or64(orv);
-  neg = __reduce_or_sync(0xffffffffu, neg);
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  if (lane == 0) {
-    s_or[warp] = orv;
-    s_neg[warp] = neg;
-  }
-  __syncthreads();
-  orv = 0;
-  neg = 0;
-  for (int w = 0; w < kYThreads / 32; ++w) {
-    orv |= s_or[w];
-    neg |= s_neg[w];
-  }
+  const uint32_t g0 = blockIdx.x * kVecGroupsPerCta;
+  uint64_t orv;
+  uint32_t neg;
+  vec_stats_stage([&](uint32_t i) { return y[i]; }, mm, g0, sm, orv, neg);
   const int b = width_from_stats(orv, neg);
   const uint64_t nw = words_for(m, b), dw = data_words(m, b);
-  if (threadIdx.x == 0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     out->stat_or = orv;
     out->stat_neg = neg;
     out->width = b;
@@ -128,7 +96,7 @@ __global__ void __launch_bounds__(kYThreads) k_mv_ypack(ccm_header* out, uint32_
     if (nw > capacity) out->status = CCM_E_CAPACITY;
   }
   if (nw > capacity) return;
-  cta_pack_groups(ys, mm, b, words, dw, nw);
+  vec_pack_groups(sm, mm, g0, b, words, dw, nw);
 }
 
 std::mutex g_attr_mutex;
@@ -153,8 +121,6 @@ size_t set_attrs() {
       dyn = umin(dyn, cap - fa.sharedSizeBytes);
   }
   for (auto fn : fns) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-  cudaFuncSetAttribute(k_mv_ypack, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)(kYSmallRows / 32 * 33 * 8));
   g_dyn_max = dyn;
   g_attr_dev = dev;
   return dyn;
@@ -242,12 +208,11 @@ void run_stream(const ccm_matrix& a, const ccm_matrix& x, const ccm_matrix& y, v
   profile_end(st);
   note_launch();
   if (m <= kYSmallRows) {
-    const size_t ysmem = (size_t)((m + 31) / 32) * 33 * 8;
+    const uint32_t g = vec_pack_ctas(m);
     if (plain)
-      k_mv_ypack<<<1, kYThreads, ysmem, st>>>(y.hdr, y.words, y.capacity,
-                                                       (const int64_t*)yv, m);
+      k_mv_ypack<<<g, kVecThreads, 0, st>>>(y.hdr, y.words, y.capacity, (const int64_t*)yv, m);
     else
-      ax::launch_pdl(k_mv_ypack, dim3(1), dim3(kYThreads), ysmem, st, y.hdr, y.words,
+      ax::launch_pdl(k_mv_ypack, dim3(g), dim3(kVecThreads), 0, st, y.hdr, y.words,
                      y.capacity, (const int64_t*)yv, m);
     note_launch();
   } else {

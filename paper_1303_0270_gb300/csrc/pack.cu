@@ -161,57 +161,27 @@ size_t pack_workspace(uint64_t rows, uint64_t cols, uint64_t capacity) {
   return (cls && n) ? ge::pack_ws_bytes(n, cls) : 0;
 }
 
-// A small dense input (n <= kSmallPack entries) packed by one CTA in one
-// launch: the header initialised, the entries read once into shared memory
-// (33 slots per 32-field group) with their width statistics, the width
-// (Eq. 1), the header, and the words (cta_pack_groups).  The general path's
-// three launches (header, statistics, pack) cost more than the work here.
+// A small dense input (n <= kSmallPack entries) packed in one launch by
+// vec_pack_ctas(n) CTAs (cta_pack.cuh): each reads all the entries for the
+// width statistics (Eq. 1) and packs its own 16 groups of 32 fields; CTA 0
+// writes the whole header.  The general path's three launches (header,
+// statistics, pack) cost more than the work here.
 constexpr uint64_t kSmallPack = 16384;
-constexpr int kSmallThreads = 1024;
 
 template <typename T>
-__global__ void __launch_bounds__(kSmallThreads) k_pack_small(const T* __restrict__ src,
-                                                              uint64_t rows, uint64_t cols,
-                                                              ccm_header* out, uint32_t* words,
-                                                              uint64_t capacity) {
-  extern __shared__ uint64_t ys[];
-  __shared__ uint64_t s_or[kSmallThreads / 32];
-  __shared__ uint32_t s_neg[kSmallThreads / 32];
+__global__ void __launch_bounds__(kVecThreads) k_pack_small(const T* __restrict__ src,
+                                                            uint64_t rows, uint64_t cols,
+                                                            ccm_header* out, uint32_t* words,
+                                                            uint64_t capacity) {
+  __shared__ VecPackSmem sm;
   const uint32_t mm = (uint32_t)(rows * cols);  // 1 .. kSmallPack
-  uint64_t orv = 0;
-  uint32_t neg = 0;
-  for (uint32_t base = 0; base < mm; base += 8 * kSmallThreads) {
-    int64_t v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {  // all eight loads in flight together
-      const uint32_t i = base + j * kSmallThreads + threadIdx.x;
-      v[j] = i < mm ? (int64_t)src[i] : 0;
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const uint32_t i = base + j * kSmallThreads + threadIdx.x;
-      if (i < mm) ys[(i >> 5) * 33 + (i & 31)] = (uint64_t)v[j];
-      orv |= fold(v[j]);
-      neg |= (uint32_t)(v[j] < 0);
-    }
-  }
-  orv = warp_or64(orv);
-  neg = __reduce_or_sync(0xffffffffu, neg);
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  if (lane == 0) {
-    s_or[warp] = orv;
-    s_neg[warp] = neg;
-  }
-  __syncthreads();
-  orv = 0;
-  neg = 0;
-  for (int w = 0; w < kSmallThreads / 32; ++w) {
-    orv |= s_or[w];
-    neg |= s_neg[w];
-  }
+  const uint32_t g0 = blockIdx.x * kVecGroupsPerCta;
+  uint64_t orv;
+  uint32_t neg;
+  vec_stats_stage([&](uint32_t i) { return (int64_t)src[i]; }, mm, g0, sm, orv, neg);
   const int b = width_from_stats(orv, neg);
   const uint64_t nw = words_for(mm, b), dw = data_words(mm, b);
-  if (threadIdx.x == 0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     out->magic = CCM_MAGIC;
     out->width = b;
     out->is_signed = neg ? 1 : 0;
@@ -225,30 +195,21 @@ __global__ void __launch_bounds__(kSmallThreads) k_pack_small(const T* __restric
     out->reserved1 = 0;
   }
   if (nw > capacity) return;
-  cta_pack_groups(ys, mm, b, words, dw, nw);
+  vec_pack_groups(sm, mm, g0, b, words, dw, nw);
 }
 
 void run_pack(const void* dense, int dtype, uint64_t rows, uint64_t cols, const ccm_matrix& out,
               void* ws, size_t ws_bytes, cudaStream_t st) {
   uint64_t n = rows * cols;
   if (n && n <= kSmallPack) {
-    const size_t smem = (size_t)((n + 31) / 32) * 33 * sizeof(uint64_t);
-    static int dev_done = -1;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev_done != dev) {
-      const int most = (int)(kSmallPack / 32 * 33 * sizeof(uint64_t));
-      cudaFuncSetAttribute(k_pack_small<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-      cudaFuncSetAttribute(k_pack_small<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-      dev_done = dev;
-    }
+    const uint32_t g = vec_pack_ctas(n);
     profile_begin(st);
     if (dtype == CCM_I64)
-      k_pack_small<int64_t><<<1, kSmallThreads, smem, st>>>((const int64_t*)dense, rows, cols,
-                                                           out.hdr, out.words, out.capacity);
+      k_pack_small<int64_t><<<g, kVecThreads, 0, st>>>((const int64_t*)dense, rows, cols,
+                                                      out.hdr, out.words, out.capacity);
     else
-      k_pack_small<int32_t><<<1, kSmallThreads, smem, st>>>((const int32_t*)dense, rows, cols,
-                                                           out.hdr, out.words, out.capacity);
+      k_pack_small<int32_t><<<g, kVecThreads, 0, st>>>((const int32_t*)dense, rows, cols,
+                                                      out.hdr, out.words, out.capacity);
     profile_end(st);
     note_launch();
     return;
