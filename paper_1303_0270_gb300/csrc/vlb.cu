@@ -218,21 +218,6 @@ __global__ void __launch_bounds__(kThreads) k_vlb_write(const T* __restrict__ sr
   }
 }
 
-// Reads `len` (<= 64) bits at bit position `pos` of the stream.
-__device__ __forceinline__ uint64_t read_bits(const uint32_t* __restrict__ w, uint64_t pos,
-                                              int len) {
-  const uint64_t wi = pos / 32;
-  const int s = (int)(pos % 32);
-  uint64_t r = (uint64_t)__ldg(w + wi) >> s;
-  int have = 32 - s;
-  if (have < len) {
-    r |= (uint64_t)__ldg(w + wi + 1) << have;
-    have += 32;
-    if (have < len) r |= (uint64_t)__ldg(w + wi + 2) << have;
-  }
-  return len >= 64 ? r : (r & ((1ull << len) - 1ull));
-}
-
 // Sequential reader of the stream from a bit position: a 64-bit buffer
 // refilled one 32-bit word at a time (one load per 32 bits consumed).
 struct BitReader {
